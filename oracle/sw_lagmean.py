@@ -1,0 +1,353 @@
+"""FP64 CPU oracle: pseudospectral rotating shallow water + Lagrangian-mean PDEs.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this module:
+only tests/, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of bench.py may use it.  It shares no code with the
+CUDA library (no kernels, headers, tables or helpers); the two meet only
+through the seeded input arrays of ``sw_inputs``.
+
+Plain and slow by design: numpy FP64, full-grid real FFTs (``numpy.fft.rfft2``
+and ``irfft2`` as library primitives), no fusion, no blocking.  Each step cites
+the passage of Kafiabad & Vanneste, "Computing Lagrangian means" (JFM 2023,
+arXiv 2208.02682) it follows.
+
+What is computed (one averaging interval [tau, tau+T], Sec. 2, Eq. (ave)):
+
+* the shallow-water dynamics, Sec. 4.2, Eq. (sw_eqs_dimless), written with
+  f0 = 1/Ro and c2 = g H = 1/Fr^2, in vector-invariant form
+  u_t = (f0 + zeta) v - d_x(c2 h + |u|^2/2), v_t = -(f0 + zeta) u - d_y(...),
+  h_t = -div(h u), zeta = d_x v - d_y u (Sec. 4.2.1 prints d_x u for the second
+  term; read as d_y u); the Laplacian viscosity is replaced by a hyperviscosity
+  -nu8 |k|^8 acting on u, v and h;
+* Strategy 1, Sec. 4.1, Eq. (gtilde-evol): (d_t + u.grad) g = f for
+  g = (t - tau) f~, with f~^L = g(tau+T)/T (Sec. 4.1);
+  mean positions from Eq. (Xi-1evol) through the periodic displacement
+  D = (t - tau)(x - Xi^{-1}), which obeys (d_t + u.grad) D = (t - tau) u (this
+  follows from Eq. (Xi-1evol) by the same substitution as Eq. (gtilde-evol);
+  the paper does not write it), so Xi^{-1}(x, tau+T) = x - D/T;
+* Strategy 2, Sec. 4.2, Eqs. (xi_evol), (barf_xi): xi = Xi - x and
+  g = (t - tau) fbar, advected by w = xi/(t - tau), forced by u and f evaluated
+  at x + xi by bilinear interpolation (Sec. 4.2.1); at t = tau, where xi = 0,
+  w takes its limit u/2 (the partial mean position is x + u s/2 + O(s^2));
+* Eulerian means, Eq. (ave): E = int f dt, mean E/T;
+* time stepping: classical RK4 with a diagonal integrating factor
+  exp(-nu |k|^8 t) (the paper's forward Euler and Heun steppers are not used);
+  the Lagrangian-mean fields share the RK stages with the dynamics (on-the-fly
+  computation, Sec. 5).
+
+Spectral convention: F_hat = rfft2(F) / N^2 on the kx >= 0 half-plane, kept only
+inside the square 2/3 box |kx|, |ky| <= K = floor((N-1)/3); physical values are
+irfft2(F_hat) * N^2 (the imaginary part on the kx = 0 column is discarded by
+the real inverse transform).
+
+Parity pins (tests/test_oracle_*.py): closed forms for a uniform inertial
+oscillation, uniform advection and the Stokes drift of a small Poincare wave,
+linear dispersion, exact mass conservation, fourth-order energy drift, PV
+material conservation, agreement of Strategies 1 and 2, and brute-force
+particle tracking with trajectory averaging (``oracle.particles``).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+LM_FIELDS = ("zeta", "h", "u", "v", "q")
+
+
+class SWOracle:
+    """Shallow-water state plus (optionally) one open averaging interval."""
+
+    _stage_hook = None  # test hook: called with each RK stage state
+
+    def __init__(self, N, dt, u, v, h, f0=1.0, c2=1.0, nu8=0.0, lm_nu8=None,
+                 model="sw", adv=(0.0, 0.0)):
+        if N % 2 or N < 8:
+            raise ValueError("N must be even and >= 8")
+        self.N = int(N)
+        self.dt = float(dt)
+        self.f0 = float(f0)
+        self.c2 = float(c2)
+        self.nu8 = float(nu8)
+        self.lm_nu8 = float(nu8 if lm_nu8 is None else lm_nu8)
+        if model not in ("sw", "kinematic"):
+            raise ValueError(model)
+        self.model = model
+        self.adv = (float(adv[0]), float(adv[1]))
+        N = self.N
+        self.K = (N - 1) // 3
+        self.kx = np.arange(N // 2 + 1, dtype=np.float64)[None, :]
+        self.ky = np.fft.fftfreq(N, d=1.0 / N)[:, None]
+        self.mask = ((self.kx <= self.K) & (np.abs(self.ky) <= self.K)).astype(np.float64)
+        self.k2 = self.kx ** 2 + self.ky ** 2
+        self.x = 2.0 * np.pi * np.arange(N) / N
+        self.t = 0.0
+        self.uh = self.spec(np.asarray(u, dtype=np.float64))
+        self.vh = self.spec(np.asarray(v, dtype=np.float64))
+        self.hh = self.spec(np.asarray(h, dtype=np.float64))
+        self.lm = None
+
+    # -- transforms --------------------------------------------------------
+    def spec(self, f):
+        """Physical -> spectral, truncated to the 2/3 box."""
+        return np.fft.rfft2(f) / float(self.N * self.N) * self.mask
+
+    def phys(self, F):
+        """Spectral -> physical values on the N x N grid."""
+        return np.fft.irfft2(F, s=(self.N, self.N)) * float(self.N * self.N)
+
+    def dx(self, F):
+        return 1j * self.kx * F
+
+    def dy(self, F):
+        return 1j * self.ky * F
+
+    # -- bilinear interpolation at x + xi (Sec. 4.2.1) ---------------------
+    def interp(self, f, xi_x, xi_y):
+        """Bilinear interpolation of the grid field f at (x_i + xi_x, y_j + xi_y).
+
+        Displacements are converted to cell units d = xi/dx; the cell index is
+        i + floor(d) (periodic) and the weight d - floor(d).
+        """
+        N = self.N
+        inv_dx = N / (2.0 * np.pi)
+        dxc = xi_x * inv_dx
+        dyc = xi_y * inv_dx
+        fx = np.floor(dxc)
+        fy = np.floor(dyc)
+        ax = dxc - fx
+        ay = dyc - fy
+        I = np.arange(N)[None, :]
+        J = np.arange(N)[:, None]
+        i0 = (I + fx.astype(np.int64)) % N
+        j0 = (J + fy.astype(np.int64)) % N
+        i1 = (i0 + 1) % N
+        j1 = (j0 + 1) % N
+        return ((1 - ax) * (1 - ay) * f[j0, i0] + ax * (1 - ay) * f[j0, i1]
+                + (1 - ax) * ay * f[j1, i0] + ax * ay * f[j1, i1])
+
+    # -- interval bookkeeping ---------------------------------------------
+    def lmean_begin(self, strategy, fields=("zeta", "h", "u", "v"), pos=True,
+                    eulerian=True, n_steps=1):
+        """Open an averaging interval at tau = current time (Sec. 2: each
+        interval [tau_n, tau_n + T] is computed independently).  Initial
+        conditions g = D = 0 (Strategy 1, g = (t - tau) f~ at t = tau) and
+        xi = g = 0 (Strategy 2, Xi(x, tau) = x)."""
+        if strategy not in (1, 2):
+            raise ValueError("strategy must be 1 or 2")
+        fields = tuple(f for f in LM_FIELDS if f in fields)
+        if strategy == 2:
+            pos = True  # xi is part of the Strategy-2 dynamics
+        z = lambda: np.zeros_like(self.uh)
+        self.lm = dict(strategy=strategy, fields=fields, pos=bool(pos),
+                       eulerian=bool(eulerian), n_steps=int(n_steps), done=0,
+                       G={f: z() for f in fields},
+                       P=[z(), z()] if pos else None,
+                       E={f: z() for f in fields} if eulerian else None)
+
+    # -- right-hand side ---------------------------------------------------
+    def _rhs(self, st, s):
+        """Right-hand sides of all evolved fields at interval time s = t - tau."""
+        if self._stage_hook is not None:
+            self._stage_hook(st)
+        uh, vh, hh = st["sw"]
+        zh = self.dx(vh) - self.dy(uh)
+        u = self.phys(uh)
+        v = self.phys(vh)
+        h = self.phys(hh)
+        zeta = self.phys(zh)
+        out = {}
+        if self.model == "sw":
+            # Eq. (sw_momentum_dimless), (sw_mass_dimless), vector-invariant form.
+            B = self.c2 * hh + self.spec(0.5 * (u * u + v * v))
+            Nu = self.f0 * vh + self.spec(zeta * v) - self.dx(B)
+            Nv = -self.f0 * uh - self.spec(zeta * u) - self.dy(B)
+            Nh = -self.dx(self.spec(h * u)) - self.dy(self.spec(h * v))
+            au, av = u, v
+            uh_adv, vh_adv = uh, vh
+        else:
+            # Passive advection of the whole state by a constant velocity.
+            cx, cy = self.adv
+            ikc = 1j * (self.kx * cx + self.ky * cy)
+            Nu, Nv, Nh = -ikc * uh, -ikc * vh, -ikc * hh
+            au = np.full((self.N, self.N), cx)
+            av = np.full((self.N, self.N), cy)
+            uh_adv, vh_adv = self.spec(au), self.spec(av)
+        out["sw"] = (Nu, Nv, Nh)
+        lm = self.lm
+        if lm is None:
+            return out
+        need_q = "q" in lm["fields"]
+        fphys = {"zeta": zeta, "h": h, "u": u, "v": v}
+        fhat = {"zeta": zh, "h": hh, "u": uh, "v": vh}
+        if need_q:
+            fphys["q"] = (self.f0 + zeta) / h  # potential vorticity, Sec. 4.2.1
+            fhat["q"] = self.spec(fphys["q"])
+        if lm["strategy"] == 1:
+            # Eq. (gtilde-evol): d_t g = f - u.grad g.
+            out["G"] = {}
+            for f in lm["fields"]:
+                G = st["G"][f]
+                adv = au * self.phys(self.dx(G)) + av * self.phys(self.dy(G))
+                out["G"][f] = fhat[f] - self.spec(adv)
+            if lm["pos"]:
+                # d_t D = s u - u.grad D (from Eq. (Xi-1evol)).
+                Dx, Dy = st["P"]
+                adx = au * self.phys(self.dx(Dx)) + av * self.phys(self.dy(Dx))
+                ady = au * self.phys(self.dx(Dy)) + av * self.phys(self.dy(Dy))
+                out["P"] = [s * uh_adv - self.spec(adx), s * vh_adv - self.spec(ady)]
+        else:
+            # Eqs. (xi_evol), (barf_xi) with w = xi/s (s > 0) or u/2 (s = 0).
+            Xx, Xy = st["P"]
+            xi_x = self.phys(Xx)
+            xi_y = self.phys(Xy)
+            if s > 0.0:
+                wx = xi_x / s
+                wy = xi_y / s
+            else:
+                wx = 0.5 * au
+                wy = 0.5 * av
+            uI = self.interp(au, xi_x, xi_y)
+            vI = self.interp(av, xi_x, xi_y)
+            wgx = wx * self.phys(self.dx(Xx)) + wy * self.phys(self.dy(Xx))
+            wgy = wx * self.phys(self.dx(Xy)) + wy * self.phys(self.dy(Xy))
+            out["P"] = [self.spec(uI - wx - wgx), self.spec(vI - wy - wgy)]
+            out["G"] = {}
+            for f in lm["fields"]:
+                G = st["G"][f]
+                fI = self.interp(fphys[f], xi_x, xi_y)
+                wg = wx * self.phys(self.dx(G)) + wy * self.phys(self.dy(G))
+                out["G"][f] = self.spec(fI - wg)
+        if lm["eulerian"]:
+            out["E"] = {f: fhat[f] for f in lm["fields"]}  # Eq. (ave)
+        return out
+
+    # -- RK4 with integrating factor ---------------------------------------
+    def _state(self):
+        st = {"sw": (self.uh, self.vh, self.hh)}
+        if self.lm is not None:
+            st["G"] = self.lm["G"]
+            if self.lm["P"] is not None:
+                st["P"] = self.lm["P"]
+            if self.lm["E"] is not None:
+                st["E"] = self.lm["E"]
+        return st
+
+    def _factors(self):
+        """Half-step integrating factors exp(L dt/2), L = -nu |k|^8."""
+        k8 = self.k2 ** 4
+        e_sw = np.exp(-self.nu8 * k8 * self.dt * 0.5)
+        e_lm = np.exp(-self.lm_nu8 * k8 * self.dt * 0.5)
+        return {"sw": e_sw, "G": e_lm, "P": e_lm, "E": np.ones_like(k8)}
+
+    @staticmethod
+    def _map(fn, *trees):
+        """Apply fn leafwise over matching state trees."""
+        t0 = trees[0]
+        if isinstance(t0, dict):
+            return {k: SWOracle._map(fn, *[t[k] for t in trees]) for k in t0}
+        if isinstance(t0, (list, tuple)):
+            return type(t0)(SWOracle._map(fn, *[t[i] for t in trees]) for i in range(len(t0)))
+        return fn(*trees)
+
+    def _efac_tree(self, st, fac):
+        return {k: self._map(lambda _x, f=fac[k]: f, v) for k, v in st.items()}
+
+    def _rk4_step(self, s0):
+        dt = self.dt
+        y = self._state()
+        E = self._efac_tree(y, self._factors())
+        m = self._map
+        a = self._rhs(y, s0)
+        y1 = m(lambda yy, aa, e: e * (yy + 0.5 * dt * aa), y, a, E)
+        b = self._rhs(y1, s0 + 0.5 * dt)
+        y2 = m(lambda yy, bb, e: e * yy + 0.5 * dt * bb, y, b, E)
+        c = self._rhs(y2, s0 + 0.5 * dt)
+        y3 = m(lambda yy, cc, e: e * e * yy + dt * e * cc, y, c, E)
+        d = self._rhs(y3, s0 + dt)
+        yn = m(lambda yy, aa, bb, cc, dd, e:
+               e * e * yy + (dt / 6.0) * (e * e * aa + 2.0 * e * (bb + cc) + dd),
+               y, a, b, c, d, E)
+        self.uh, self.vh, self.hh = yn["sw"]
+        if self.lm is not None:
+            self.lm["G"] = yn["G"]
+            if "P" in yn:
+                self.lm["P"] = yn["P"]
+            if "E" in yn:
+                self.lm["E"] = yn["E"]
+        self.t += dt
+
+    def step(self, nsteps):
+        """Advance the dynamics only (no interval open)."""
+        if self.lm is not None:
+            raise RuntimeError("an averaging interval is open")
+        for _ in range(int(nsteps)):
+            self._rk4_step(0.0)
+
+    def lmean_step(self, nsteps):
+        lm = self.lm
+        if lm is None:
+            raise RuntimeError("no averaging interval open")
+        if lm["done"] + nsteps > lm["n_steps"]:
+            raise ValueError("more steps than remain in the interval")
+        for _ in range(int(nsteps)):
+            # s = t - tau counted in whole steps (never accumulated).
+            self._rk4_step(lm["done"] * self.dt)
+            lm["done"] += 1
+
+    def lmean_end(self):
+        """Close the interval; total means as physical FP64 fields.
+
+        Strategy 1: f~^L = g/T and Xi^{-1}(x, tau+T) = x - D/T (Sec. 4.1).
+        Strategy 2: fbar^L = g/T and Xi(x, tau+T) = x + xi (Sec. 3.2, 4.2).
+        Eulerian: E/T (Eq. (ave)).
+        """
+        lm = self.lm
+        if lm is None or lm["done"] != lm["n_steps"]:
+            raise RuntimeError("interval not complete")
+        T = lm["n_steps"] * self.dt
+        out = {}
+        for f in lm["fields"]:
+            out[f] = self.phys(lm["G"][f]) / T
+        X = self.x[None, :] + 0.0 * self.x[:, None]
+        Y = self.x[:, None] + 0.0 * self.x[None, :]
+        if lm["pos"]:
+            if lm["strategy"] == 1:
+                dxp = self.phys(lm["P"][0]) / T
+                dyp = self.phys(lm["P"][1]) / T
+                out["pos_x"] = X - dxp
+                out["pos_y"] = Y - dyp
+            else:
+                out["pos_x"] = X + self.phys(lm["P"][0])
+                out["pos_y"] = Y + self.phys(lm["P"][1])
+        if lm["eulerian"]:
+            for f in lm["fields"]:
+                out["E_" + f] = self.phys(lm["E"][f]) / T
+        self.lm = None
+        return out
+
+    # -- diagnostics -------------------------------------------------------
+    def fields(self):
+        return self.phys(self.uh), self.phys(self.vh), self.phys(self.hh)
+
+    def diag(self):
+        """Domain means: mass <h>, energy <h|u|^2/2 + c2 h^2/2>, potential
+        enstrophy <h q^2/2> with q = (f0 + zeta)/h."""
+        u, v, h = self.fields()
+        zeta = self.phys(self.dx(self.vh) - self.dy(self.uh))
+        q = (self.f0 + zeta) / h
+        return (float(np.mean(h)),
+                float(np.mean(0.5 * h * (u * u + v * v) + 0.5 * self.c2 * h * h)),
+                float(np.mean(0.5 * h * q * q)))
+
+    def spectral_state(self):
+        """Copy of the spectral SW state (kx >= 0 half-plane arrays)."""
+        return self.uh.copy(), self.vh.copy(), self.hh.copy()
+
+
+def rel_l2(a, b):
+    """||a - b||_2 / ||b||_2 over the grid."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = math.sqrt(float(np.sum(b * b)))
+    return math.sqrt(float(np.sum((a - b) ** 2))) / (nb if nb > 0 else 1.0)
