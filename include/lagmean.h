@@ -1,0 +1,192 @@
+/*
+ * lagmean.h -- C ABI of the GB300 library for on-the-fly Lagrangian means of a
+ * doubly periodic pseudospectral rotating shallow-water flow.
+ *
+ * Method: Kafiabad & Vanneste, "Computing Lagrangian means" (JFM 2023,
+ * arXiv 2208.02682).  The library advances the shallow-water equations
+ * (Sec. 4.2, Eq. (sw_eqs_dimless), with f0 = 1/Ro, c2 = gH = 1/Fr^2 and a
+ * hyperviscosity -nu8 |k|^8 in place of the Laplacian) together with the
+ * Lagrangian-mean PDEs of one averaging interval [tau, tau + T]:
+ *   Strategy 1 (Sec. 3.1, 4.1): Eq. (gtilde-evol), (d_t + u.grad) g = f with
+ *     g = (t - tau) f~, and the mean positions Xi^{-1} of Eq. (Xi-1evol)
+ *     carried as the periodic displacement D = (t - tau)(x - Xi^{-1});
+ *   Strategy 2 (Sec. 3.2, 4.2): Eqs. (xi_evol), (barf_xi) for the displacement
+ *     xi = Xi - x and g = (t - tau) fbar, with u and f interpolated bilinearly
+ *     at x + xi;
+ *   Eulerian means, Eq. (ave).
+ * Intervals are computed one after another, each from its own zero state
+ * (Sec. 2: tau_n = n T).  Time stepping is classical RK4 with an integrating
+ * factor for the hyperviscosity; all fields share the RK stages.
+ *
+ * Conventions
+ *  - Grid: N x N points on [0, 2 pi)^2, N a power of two in [16, 2048];
+ *    x_i = 2 pi i / N.  Physical arrays are row-major with y the slow index:
+ *    a[j * N + i] is the value at (x_i, y_j).
+ *  - Every call returns an int status (SW_OK = 0).  No C++ exception crosses
+ *    the ABI.  sw_last_error() gives a message for the last failing call on a
+ *    handle.  A NULL handle argument gives SW_EINVAL (sw_destroy: no-op).
+ *  - Device work is issued asynchronously on the stream given to sw_create
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    Calls that return data to host memory synchronise that stream.
+ *  - One host thread at a time per handle.  The library owns all device
+ *    memory of a handle; sw_destroy releases it.
+ *  - Precision: SW_PREC_FP64 runs every step in FP64.  SW_PREC_FP32 runs the
+ *    transforms, products and advection in FP32 with compensated (Kahan)
+ *    summation of the Lagrangian-mean and Eulerian accumulators; the
+ *    end-of-interval division, mean-position recovery, initial transform and
+ *    invariant reductions are FP64 in both modes.
+ */
+#ifndef LAGMEAN_H
+#define LAGMEAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SW_OK 0
+#define SW_EINVAL 1   /* invalid argument (value given in sw_last_error)      */
+#define SW_ENOMEM 2   /* device or host allocation failed                      */
+#define SW_EBUSY 3    /* sw_step while an averaging interval is open           */
+#define SW_ERANGE 4   /* more steps than remain in the open interval           */
+#define SW_ESTATE 5   /* call not valid in the handle's current state          */
+#define SW_ETIMEOUT 6 /* a bounded device wait gave up                         */
+#define SW_ECUDA 7    /* a CUDA runtime call failed (message in sw_last_error) */
+
+/* ---- enumerations ------------------------------------------------------- */
+#define SW_PREC_FP64 0
+#define SW_PREC_FP32 1
+
+#define SW_MODEL_SW 0        /* rotating shallow water, Eq. (sw_eqs_dimless) */
+#define SW_MODEL_KINEMATIC 1 /* test model: the state is passively advected
+                                by the constant velocity (adv_x, adv_y), and
+                                the Lagrangian-mean equations see u = adv   */
+
+/* Lagrangian-mean field mask (lm_params.fields) */
+#define LM_ZETA 1 /* relative vorticity zeta = d_x v - d_y u              */
+#define LM_H 2    /* depth h                                             */
+#define LM_U 4    /* velocity u                                          */
+#define LM_V 8    /* velocity v                                          */
+#define LM_Q 16   /* potential vorticity q = (f0 + zeta)/h (Sec. 4.2.1)  */
+#define LM_POS 32 /* mean positions (always on for Strategy 2)            */
+
+typedef struct sw_handle sw_handle;
+
+/* Model and discretisation parameters (sw_create). */
+typedef struct sw_params {
+  int32_t N;         /* grid points per side: power of two, 16..2048        */
+  int32_t precision; /* SW_PREC_FP64 or SW_PREC_FP32                        */
+  int32_t model;     /* SW_MODEL_SW or SW_MODEL_KINEMATIC                    */
+  int32_t reserved;  /* must be 0                                           */
+  double dt;         /* RK4 time step, > 0                                  */
+  double f0;         /* Coriolis parameter (1/Ro)                           */
+  double c2;         /* squared gravity-wave speed g H (1/Fr^2), >= 0        */
+  double nu8;        /* hyperviscosity on u, v, h: -nu8 |k|^8, >= 0          */
+  double lm_nu8;     /* hyperviscosity on the Lagrangian-mean fields, >= 0   */
+  double adv_x;      /* advection velocity of SW_MODEL_KINEMATIC            */
+  double adv_y;
+} sw_params;
+
+/* One averaging interval (lmean_begin). */
+typedef struct lm_params {
+  int32_t strategy; /* 1 or 2                                               */
+  int32_t fields;   /* LM_* mask; at least one of ZETA,H,U,V,Q or POS       */
+  int32_t eulerian; /* nonzero: also accumulate Eulerian means of `fields`   */
+  int32_t reserved; /* must be 0                                            */
+  int64_t n_steps;  /* interval length T = n_steps * dt, >= 1               */
+} lm_params;
+
+/* Outputs of lmean_end: FP64 physical N x N arrays, caller-owned.  A NULL
+ * pointer skips that output.  Fields not in the interval's mask must be NULL.
+ * Strategy 1: zeta..q = f~^L = g(tau+T)/T indexed by the end position x,
+ *   pos = Xi^{-1}(x, tau+T) = x - D/T (the mean position of the particle
+ *   that is at x at tau+T); Strategy 2: zeta..q = fbar^L indexed by the mean
+ *   position x, pos = Xi(x, tau+T) = x + xi.  e_* = Eulerian means E/T. */
+typedef struct lm_result {
+  double *zeta, *h, *u, *v, *q;
+  double *pos_x, *pos_y;
+  double *e_zeta, *e_h, *e_u, *e_v, *e_q;
+  int32_t on_device; /* 1: all pointers are device memory; 0: host memory */
+  int32_t reserved;
+} lm_result;
+
+/* Create a handle from a physical initial condition.
+ * ic_uvh: 3*N*N doubles (u, then v, then h), host memory if ic_on_device == 0
+ * else device memory; copied, not retained.  The fields are transformed and
+ * truncated to the 2/3 box |kx|, |ky| <= floor((N-1)/3).
+ * stream: cudaStream_t for all device work of this handle (NULL: default).
+ * Errors: SW_EINVAL (bad parameter), SW_ENOMEM, SW_ECUDA.  On error *out is
+ * set to NULL and nothing is leaked. */
+int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_device,
+              void* stream, sw_handle** out);
+
+/* Release all memory of a handle (synchronises its stream).  NULL: no-op. */
+void sw_destroy(sw_handle* h);
+
+/* Advance the shallow-water state only by nsteps >= 0 RK4 steps.
+ * SW_EBUSY while an averaging interval is open.  Asynchronous. */
+int sw_step(sw_handle* h, int64_t nsteps);
+
+/* Open an averaging interval at tau = current time: zero the Lagrangian-mean
+ * state (g = D = 0, or xi = g = 0, Sec. 3.1-3.2 initial conditions; Eulerian
+ * accumulators = 0).  SW_ESTATE if an interval is already open. */
+int lmean_begin(sw_handle* h, const lm_params* lp);
+
+/* Advance the dynamics and the open interval together by nsteps >= 0 RK4
+ * steps (on-the-fly computation, Sec. 5).  SW_ERANGE if nsteps exceeds the
+ * steps remaining, SW_ESTATE if no interval is open.  Asynchronous: the
+ * steps are replays of a captured CUDA graph on the handle's stream. */
+int lmean_step(sw_handle* h, int64_t nsteps);
+
+/* Close a completed interval (remaining steps == 0, else SW_ESTATE) and write
+ * the means (see lm_result) in FP64.  Synchronises the handle's stream. */
+int lmean_end(sw_handle* h, const lm_result* out);
+
+/* Steps remaining in the open interval (0 if none) and steps done. */
+int lmean_progress(sw_handle* h, int64_t* done, int64_t* remaining);
+
+/* Physical FP64 u, v, h of the current state into uvh (3*N*N doubles, host
+ * if on_device == 0).  Synchronises. */
+int sw_get_fields(sw_handle* h, double* uvh, int on_device);
+
+/* Replace the shallow-water state by a physical initial condition (as in
+ * sw_create).  SW_EBUSY while an interval is open. */
+int sw_set_fields(sw_handle* h, const double* uvh, int on_device);
+
+/* Invariants in FP64 with a deterministic reduction order:
+ * out[0] = mass <h> (the k = 0 depth coefficient),
+ * out[1] = energy <h |u|^2/2 + c2 h^2/2>,
+ * out[2] = potential enstrophy <h q^2/2>, q = (f0 + zeta)/h.
+ * Means over the N x N grid.  Synchronises. */
+int sw_diag(sw_handle* h, double out[3]);
+
+/* Checkpoint of the complete state (dynamics, open interval, compensation
+ * terms, step counters) as an opaque blob.  Call with blob == NULL to get
+ * the size in *size; then with a buffer of at least that size.  Restoring
+ * with sw_set_state on a handle created with the same sw_params continues
+ * bit-for-bit as if uninterrupted.  SW_EINVAL on a size or parameter
+ * mismatch. */
+int sw_get_state(sw_handle* h, void* blob, size_t* size);
+int sw_set_state(sw_handle* h, const void* blob, size_t size);
+
+/* Model time of the current state (dt * steps taken since creation). */
+int sw_time(sw_handle* h, double* t);
+
+/* Wait for all device work of the handle. */
+int sw_sync(sw_handle* h);
+
+/* Message for the last failing call on h ("" if none); valid until the next
+ * call on h.  With h == NULL, the message of the last failing sw_create. */
+const char* sw_last_error(sw_handle* h);
+
+/* Library version string. */
+const char* sw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAGMEAN_H */

@@ -1,0 +1,13 @@
+"""GB300 library for on-the-fly Lagrangian means of rotating shallow water
+(Kafiabad & Vanneste, "Computing Lagrangian means", arXiv 2208.02682).
+
+The compute path is liblagmean.so (CUDA for sm_103a) behind the C ABI of
+include/lagmean.h; ``api`` is its thin ctypes binding.
+"""
+from ._build import build  # noqa: F401
+from . import api  # noqa: F401
+from .api import (  # noqa: F401
+    SWError, make_params, make_lm_params, sw_create, sw_destroy, sw_step, lmean_begin,
+    lmean_step, lmean_end, lmean_progress, sw_get_fields, sw_set_fields, sw_diag,
+    sw_get_state, sw_set_state, sw_time, sw_sync, sw_last_error, sw_version,
+)

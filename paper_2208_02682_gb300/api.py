@@ -1,0 +1,248 @@
+"""Thin Python binding of the C ABI in include/lagmean.h (ctypes).
+
+Same names as the C entry points; this module only marshals arguments.  All
+computation happens in liblagmean.so (CUDA, sm_103a).  Loading fails loudly
+when the library is missing: there is no CPU fallback.
+
+Host arrays are numpy float64 C-contiguous; device arrays are torch CUDA
+float64 tensors (only their data pointers cross the ABI).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblagmean.so")
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_EBUSY, SW_ERANGE, SW_ESTATE, SW_ETIMEOUT, SW_ECUDA = range(8)
+SW_PREC_FP64, SW_PREC_FP32 = 0, 1
+SW_MODEL_SW, SW_MODEL_KINEMATIC = 0, 1
+LM_ZETA, LM_H, LM_U, LM_V, LM_Q, LM_POS = 1, 2, 4, 8, 16, 32
+FIELD_BITS = {"zeta": LM_ZETA, "h": LM_H, "u": LM_U, "v": LM_V, "q": LM_Q}
+
+EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "lmean_end",
+           "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
+           "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version")
+
+
+class sw_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32),
+                ("reserved", C.c_int32), ("dt", C.c_double), ("f0", C.c_double),
+                ("c2", C.c_double), ("nu8", C.c_double), ("lm_nu8", C.c_double),
+                ("adv_x", C.c_double), ("adv_y", C.c_double)]
+
+
+class lm_params(C.Structure):
+    _fields_ = [("strategy", C.c_int32), ("fields", C.c_int32), ("eulerian", C.c_int32),
+                ("reserved", C.c_int32), ("n_steps", C.c_int64)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class lm_result(C.Structure):
+    _fields_ = [("zeta", _DP), ("h", _DP), ("u", _DP), ("v", _DP), ("q", _DP),
+                ("pos_x", _DP), ("pos_y", _DP),
+                ("e_zeta", _DP), ("e_h", _DP), ("e_u", _DP), ("e_v", _DP), ("e_q", _DP),
+                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lagmean error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblagmean.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2208_02682_gb300.build()")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    sig = {
+        "sw_create": (C.c_int, [C.POINTER(sw_params), _DP, C.c_int, C.c_void_p, C.POINTER(H)]),
+        "sw_destroy": (None, [H]),
+        "sw_step": (C.c_int, [H, C.c_int64]),
+        "lmean_begin": (C.c_int, [H, C.POINTER(lm_params)]),
+        "lmean_step": (C.c_int, [H, C.c_int64]),
+        "lmean_end": (C.c_int, [H, C.POINTER(lm_result)]),
+        "lmean_progress": (C.c_int, [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "sw_get_fields": (C.c_int, [H, _DP, C.c_int]),
+        "sw_set_fields": (C.c_int, [H, _DP, C.c_int]),
+        "sw_diag": (C.c_int, [H, _DP]),
+        "sw_get_state": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_size_t)]),
+        "sw_set_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
+        "sw_time": (C.c_int, [H, _DP]),
+        "sw_sync": (C.c_int, [H]),
+        "sw_last_error": (C.c_char_p, [H]),
+        "sw_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, h):
+    if rc != SW_OK:
+        msg = load().sw_last_error(h)
+        raise SWError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy float64 array or a torch CUDA tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data_as(_DP), 0
+    # torch tensor
+    if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+        raise ValueError("device tensors must be contiguous float64")
+    return C.cast(C.c_void_p(a.data_ptr()), _DP), 1 if a.is_cuda else 0
+
+
+def make_params(N, dt, precision="f64", model="sw", f0=1.0, c2=1.0, nu8=0.0, lm_nu8=None,
+                adv=(0.0, 0.0)) -> sw_params:
+    p = sw_params()
+    p.N = int(N)
+    p.precision = {"f64": SW_PREC_FP64, "f32": SW_PREC_FP32}[precision]
+    p.model = {"sw": SW_MODEL_SW, "kinematic": SW_MODEL_KINEMATIC}[model]
+    p.reserved = 0
+    p.dt, p.f0, p.c2, p.nu8 = float(dt), float(f0), float(c2), float(nu8)
+    p.lm_nu8 = float(nu8 if lm_nu8 is None else lm_nu8)
+    p.adv_x, p.adv_y = float(adv[0]), float(adv[1])
+    return p
+
+
+def make_lm_params(strategy, fields=("zeta", "h", "u", "v"), pos=True, eulerian=True,
+                   n_steps=1) -> lm_params:
+    lp = lm_params()
+    lp.strategy = int(strategy)
+    bits = 0
+    for f in fields:
+        bits |= FIELD_BITS[f]
+    if pos:
+        bits |= LM_POS
+    lp.fields = bits
+    lp.eulerian = 1 if eulerian else 0
+    lp.reserved = 0
+    lp.n_steps = int(n_steps)
+    return lp
+
+
+# ---- same names as the C ABI --------------------------------------------------
+def sw_create(params: sw_params, ic_uvh, stream=None):
+    """Create a handle; ic_uvh: (3, N, N) float64 host array or CUDA tensor."""
+    lib = load()
+    ptr, dev = _ptr(ic_uvh)
+    h = C.c_void_p()
+    rc = lib.sw_create(C.byref(params), ptr, dev, C.c_void_p(stream or 0), C.byref(h))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return h
+
+
+def sw_destroy(h):
+    load().sw_destroy(h)
+
+
+def sw_step(h, nsteps):
+    _check(load().sw_step(h, int(nsteps)), h)
+
+
+def lmean_begin(h, lp: lm_params):
+    _check(load().lmean_begin(h, C.byref(lp)), h)
+
+
+def lmean_step(h, nsteps):
+    _check(load().lmean_step(h, int(nsteps)), h)
+
+
+def lmean_progress(h):
+    d, r = C.c_int64(), C.c_int64()
+    _check(load().lmean_progress(h, C.byref(d), C.byref(r)), h)
+    return d.value, r.value
+
+
+RESULT_KEYS = ("zeta", "h", "u", "v", "q", "pos_x", "pos_y", "e_zeta", "e_h", "e_u", "e_v", "e_q")
+
+
+def lmean_end(h, out: dict):
+    """out: dict key -> array (see RESULT_KEYS); all host or all device."""
+    r = lm_result()
+    ondev = set()
+    for k in RESULT_KEYS:
+        a = out.get(k)
+        p, d = _ptr(a)
+        if a is not None:
+            ondev.add(d)
+            setattr(r, k, p)
+    if len(ondev) > 1:
+        raise ValueError("outputs must be all host or all device")
+    r.on_device = ondev.pop() if ondev else 0
+    r.reserved = 0
+    _check(load().lmean_end(h, C.byref(r)), h)
+    return out
+
+
+def sw_get_fields(h, uvh):
+    p, d = _ptr(uvh)
+    _check(load().sw_get_fields(h, p, d), h)
+    return uvh
+
+
+def sw_set_fields(h, uvh):
+    p, d = _ptr(uvh)
+    _check(load().sw_set_fields(h, p, d), h)
+
+
+def sw_diag(h):
+    out = (C.c_double * 3)()
+    _check(load().sw_diag(h, out), h)
+    return tuple(out)
+
+
+def sw_get_state(h) -> bytes:
+    lib = load()
+    n = C.c_size_t(0)
+    _check(lib.sw_get_state(h, None, C.byref(n)), h)
+    buf = C.create_string_buffer(n.value)
+    _check(lib.sw_get_state(h, buf, C.byref(n)), h)
+    return buf.raw[: n.value]
+
+
+def sw_set_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().sw_set_state(h, buf, len(blob)), h)
+
+
+def sw_time(h):
+    t = C.c_double()
+    _check(load().sw_time(h, C.byref(t)), h)
+    return t.value
+
+
+def sw_sync(h):
+    _check(load().sw_sync(h), h)
+
+
+def sw_last_error(h=None):
+    m = load().sw_last_error(h)
+    return m.decode() if m else ""
+
+
+def sw_version():
+    return load().sw_version().decode()

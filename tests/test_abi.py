@@ -1,0 +1,76 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol the header declares, the binding's structs match the C layout, and
+argument validation happens before any device call."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lagmean.h")
+
+
+@pytest.fixture(scope="module")
+def lm():
+    import paper_2208_02682_gb300 as lm
+    lm.build()
+    lm.api.load()
+    return lm
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**\s*(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("sw_create", "sw_step", "lmean_begin", "lmean_step", "lmean_end", "sw_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lm):
+    lib = C.CDLL(lm.api.LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert set(lm.api.EXPORTS) == set(declared_functions())
+
+
+def test_struct_layout_matches_c(tmp_path, lm):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include "lagmean.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                    "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(sw_params),"
+                    " sizeof(lm_params), sizeof(lm_result), offsetof(sw_params, dt),"
+                    " offsetof(lm_result, on_device)); return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    api = lm.api
+    assert got == [C.sizeof(api.sw_params), C.sizeof(api.lm_params), C.sizeof(api.lm_result),
+                   api.sw_params.dt.offset, api.lm_result.on_device.offset]
+
+
+@pytest.mark.parametrize("field,value", [("N", 48), ("N", 8), ("N", 4096), ("dt", 0.0), ("dt", -1.0),
+                                         ("precision", 7), ("model", 3), ("nu8", -1.0),
+                                         ("c2", float("nan")), ("reserved", 1)])
+def test_invalid_parameters_rejected_before_device_use(lm, field, value):
+    p = lm.make_params(64, 1e-3)
+    setattr(p, field, value)
+    ic = np.zeros((3, 64, 64))
+    with pytest.raises(lm.SWError) as ei:
+        lm.sw_create(p, ic)
+    assert ei.value.code == lm.api.SW_EINVAL
+    assert lm.sw_last_error(None)
+
+
+def test_null_handle_is_rejected(lm):
+    lib = lm.api.load()
+    assert lib.sw_step(None, 1) == lm.api.SW_EINVAL
+    assert lib.lmean_step(None, 1) == lm.api.SW_EINVAL
+    assert lib.lmean_begin(None, None) == lm.api.SW_EINVAL
+    assert lib.sw_sync(None) == lm.api.SW_EINVAL
+    lib.sw_destroy(None)  # no-op
