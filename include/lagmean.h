@@ -142,7 +142,9 @@ int lmean_begin(sw_handle* h, const lm_params* lp);
 int lmean_step(sw_handle* h, int64_t nsteps);
 
 /* Close a completed interval (remaining steps == 0, else SW_ESTATE) and write
- * the means (see lm_result) in FP64.  Synchronises the handle's stream. */
+ * the means (see lm_result) in FP64.  With host outputs it synchronises the
+ * handle's stream; with device outputs (on_device = 1) it returns once the
+ * work is enqueued on that stream. */
 int lmean_end(sw_handle* h, const lm_result* out);
 
 /* Steps remaining in the open interval (0 if none) and steps done. */
@@ -174,6 +176,30 @@ int sw_set_state(sw_handle* h, const void* blob, size_t size);
 
 /* Model time of the current state (dt * steps taken since creation). */
 int sw_time(sw_handle* h, double* t);
+
+/* Kernel classes reported by sw_kernel_times. */
+#define SW_K_COL_INV 0  /* column pass: spectral -> mixed (derivatives, inverse y-FFT) */
+#define SW_K_ROW_INV 1  /* row pass: mixed -> physical gather buffer (Strategy 2)   */
+#define SW_K_ROW_PROD 2 /* row pass: inverse x-FFT, products, forward x-FFT        */
+#define SW_K_COL_FWD 3  /* column pass: forward y-FFT and 2/3 mask                  */
+#define SW_K_UPDATE 4   /* right-hand sides and RK4 integrating-factor update       */
+#define SW_K_PHYS_Q 5   /* potential vorticity in the gather buffer (Strategy 2)    */
+#define SW_K_COUNT 8
+
+/* Per-kernel device times of the stepping kernels.  Runs nsteps >= 1 RK4
+ * steps of the current configuration (dynamics only, or the open interval,
+ * whose remaining steps must allow it), advancing the state exactly as
+ * sw_step / lmean_step do, but with each kernel launched on its own and
+ * bracketed by CUDA events on the handle's stream.  For each class k:
+ * ms[k] = summed device milliseconds, launches[k] = launches, bytes[k] =
+ * summed algorithmic bytes (the distinct inputs each launch must read and the
+ * outputs it must write; L2 hits are not subtracted).  Synchronises. */
+int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUNT],
+                    int64_t launches[SW_K_COUNT], double bytes[SW_K_COUNT]);
+
+/* Number of CUDA kernels this handle has launched since creation (graph
+ * replays count each kernel node). */
+int sw_launch_count(sw_handle* h, int64_t* count);
 
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);

@@ -25,7 +25,10 @@ FIELD_BITS = {"zeta": LM_ZETA, "h": LM_H, "u": LM_U, "v": LM_V, "q": LM_Q}
 
 EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "lmean_end",
            "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
-           "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version")
+           "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version", "sw_kernel_times",
+           "sw_launch_count")
+SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
+SW_K_COUNT = 8
 
 
 class sw_params(C.Structure):
@@ -84,6 +87,8 @@ def load(path: str = LIB_PATH):
         "sw_time": (C.c_int, [H, _DP]),
         "sw_sync": (C.c_int, [H]),
         "sw_last_error": (C.c_char_p, [H]),
+        "sw_kernel_times": (C.c_int, [H, C.c_int64, _DP, C.POINTER(C.c_int64), _DP]),
+        "sw_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "sw_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +242,22 @@ def sw_time(h):
 
 def sw_sync(h):
     _check(load().sw_sync(h), h)
+
+
+def sw_kernel_times(h, nsteps):
+    """{kernel: (total_ms, launches, total_algorithmic_bytes)} over nsteps
+    RK4 steps launched kernel by kernel (advances the state)."""
+    ms = (C.c_double * SW_K_COUNT)()
+    nl = (C.c_int64 * SW_K_COUNT)()
+    by = (C.c_double * SW_K_COUNT)()
+    _check(load().sw_kernel_times(h, int(nsteps), ms, nl, by), h)
+    return {name: (ms[k], nl[k], by[k]) for k, name in enumerate(SW_K_NAMES) if nl[k] > 0}
+
+
+def sw_launch_count(h):
+    n = C.c_int64()
+    _check(load().sw_launch_count(h, C.byref(n)), h)
+    return n.value
 
 
 def sw_last_error(h=None):

@@ -69,6 +69,8 @@ enum {
 };
 // integrating-factor classes
 enum { IF_DYN = 0, IF_LM = 1, IF_NONE = 2 };
+// role of an evolved field in the right-hand side
+enum { R_U = 0, R_V = 1, R_H = 2, R_G = 3, R_P = 4, R_E = 5 };
 
 struct Layout {
   int strategy;   // 0: dynamics only, 1 or 2
@@ -86,6 +88,8 @@ struct Layout {
   int f_e[NLMF];     // Eulerian accumulators per LM slot
   int fclass[MAXF];  // IF_* class of each evolved field
   int fkahan[MAXF];  // compensated final update (FP32 mode) for this field
+  int frole[MAXF];   // R_* role
+  int fslot[MAXF];   // LM slot (R_G, R_E) or component (R_P)
   // column pass: output i = op(src[i] (, src2[i]))
   int i_src[MAXI], i_src2[MAXI], i_op[MAXI];
   int i_u, i_v, i_h, i_z;      // dynamics intermediates

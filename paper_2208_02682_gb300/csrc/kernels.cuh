@@ -288,8 +288,9 @@ __device__ __forceinline__ T bilinear(const T* __restrict__ f, int i, int j, T x
 }
 
 // ---------------------------------------------------------------------------
-// Row pass with products.  Smem: W, P (B*pad8(N) complex each), U (4*B*N
-// reals: u, v, h, zeta), XI (2*B*N reals, Strategy 2).
+// Row pass with products.  grid (N/B, ceil(npairs/ppb)): block (x, y) owns B
+// rows and product pairs [y*ppb, (y+1)*ppb).  Smem: W, P (B*pad8(N) complex
+// each), U (4*B*N reals: u, v, h, zeta), XI (2*B*N reals, Strategy 2).
 template <typename T>
 struct RowProdArgs {
   const cplx<T>* mix;   // column-pass outputs, stride mi
@@ -300,7 +301,8 @@ struct RowProdArgs {
   Geom g;
   Layout L;
   StepConsts c;
-  int B;
+  int B;    // rows per block
+  int ppb;  // product pairs per block
   int stage;
 };
 
@@ -316,6 +318,8 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
   T* U = reinterpret_cast<T*>(P + B * bst);
   T* XI = U + 4 * B * N;
   const int row0 = blockIdx.x * B;
+  const int p0 = blockIdx.y * a.ppb * 2;
+  const int p1 = min(L.np, p0 + a.ppb * 2);
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int BN = B * N;
   const bool kin = L.model == 1;
@@ -326,6 +330,14 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
   const T inv_s = s0 ? (T)0 : (T)(1.0 / s);
   const T inv_dx = (T)((double)N / 6.283185307179586476925286766559);
 
+  // which physical base fields this block's products read
+  bool need_uv = false, need_hz = false;
+  for (int p = p0; p < p1; ++p) {
+    const int k = L.pk[p];
+    if (k == PK_ZV || k == PK_ZU || k == PK_HU || k == PK_HV || k == PK_Q) need_hz = true;
+    if (k == PK_ZV || k == PK_ZU || k == PK_KE || k == PK_HU || k == PK_HV) need_uv = true;
+    if ((k == PK_ADV || k == PK_XI || k == PK_GBAR) && !kin) need_uv = true;
+  }
   // phase 0: physical u, v, h, zeta of the block's rows
   if (L.strategy == 2) {
     for (int e = tid; e < BN; e += nthr) {
@@ -342,21 +354,26 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
       XI[BN + e] = v.y;
     }
   } else {
-    row_pair_inverse<T>(W, a.mix + (long long)L.i_u * g.mi, a.mix + (long long)L.i_v * g.mi, row0, B, g,
-                        a.tw);
-    for (int e = tid; e < BN; e += nthr) {
-      const int r = e / N, x = e - r * N;
-      const cplx<T> v = W[r * bst + pad8(x)];
-      U[e] = v.x;
-      U[BN + e] = v.y;
+    if (need_uv) {
+      row_pair_inverse<T>(W, a.mix + (long long)L.i_u * g.mi, a.mix + (long long)L.i_v * g.mi, row0, B, g,
+                          a.tw);
+      for (int e = tid; e < BN; e += nthr) {
+        const int r = e / N, x = e - r * N;
+        const cplx<T> v = W[r * bst + pad8(x)];
+        U[e] = v.x;
+        U[BN + e] = v.y;
+      }
+      __syncthreads();
     }
-    row_pair_inverse<T>(W, a.mix + (long long)L.i_h * g.mi, a.mix + (long long)L.i_z * g.mi, row0, B, g,
-                        a.tw);
-    for (int e = tid; e < BN; e += nthr) {
-      const int r = e / N, x = e - r * N;
-      const cplx<T> v = W[r * bst + pad8(x)];
-      U[2 * BN + e] = v.x;
-      U[3 * BN + e] = v.y;
+    if (need_hz) {
+      row_pair_inverse<T>(W, a.mix + (long long)L.i_h * g.mi, a.mix + (long long)L.i_z * g.mi, row0, B, g,
+                          a.tw);
+      for (int e = tid; e < BN; e += nthr) {
+        const int r = e / N, x = e - r * N;
+        const cplx<T> v = W[r * bst + pad8(x)];
+        U[2 * BN + e] = v.x;
+        U[3 * BN + e] = v.y;
+      }
     }
   }
   __syncthreads();
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
   // products, two at a time through the forward FFT
   int slot = 0;
   int pend = -1;
-  for (int p = 0; p < L.np; ++p) {
+  for (int p = p0; p < p1; ++p) {
     const int kind = L.pk[p];
     const bool need_grad = kind == PK_ADV || kind == PK_XI || kind == PK_GBAR;
     if (need_grad) {
@@ -439,12 +456,14 @@ __global__ void k_phys_q(T* phys, long long np, double f0) {
 //   stage 1: b = N(y1)       acc += 2 E b           y2 = E y_n + dt/2 b
 //   stage 2: c = N(y2)       acc += 2 E c           y3 = E^2 y_n + dt E c
 //   stage 3: d = N(y3)       y_{n+1} = E^2 y_n + dt/6 (acc + d)
-// with E = exp(-nu |k|^8 dt/2).  The stage input ys is read before it is
-// overwritten by the next stage input (same mode, same thread).
+// with E = exp(-nu |k|^8 dt/2).  Stage inputs alternate between two buffers:
+// a thread reads other fields' stage inputs at its mode, so the next stage's
+// values go to the other buffer.
 template <typename T>
 struct UpdateArgs {
-  cplx<T>* y;     // state at t_n
-  cplx<T>* ys;    // stage input (stage 0: unused, y is the input)
+  cplx<T>* y;           // state at t_n
+  const cplx<T>* ysin;  // stage input (stage 0: unused, y is the input)
+  cplx<T>* ys;          // next stage input (stages 0-2); never aliases ysin
   cplx<T>* acc;
   cplx<T>* comp;  // Kahan compensation (FP32 mode), may be null
   const cplx<T>* ps;  // spectral products
@@ -478,97 +497,100 @@ __device__ __forceinline__ double kahan_add_rn(double sum, double add, double& c
   return t;
 }
 
+// One thread per (mode, evolved field): grid (ceil(ms/256), nf).
 template <typename T>
 __global__ void __launch_bounds__(256) k_update(const __grid_constant__ UpdateArgs<T> a) {
   const Geom& g = a.g;
   const Layout& L = a.L;
   const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
   const double sd = stage_time(a.ctr, a.stage, a.c.dt);
   if (m < g.ms) {
     const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
     if (kx <= g.K) {
       const T kxf = (T)kx, kyf = (T)(kyi - g.K);
       const T dt = (T)a.c.dt;
-      const cplx<T>* yin = a.stage == 0 ? a.y : a.ys;
-      cplx<T> x[MAXF], rhs[MAXF];
-      for (int f = 0; f < L.nf; ++f) x[f] = yin[f * g.ms + m];
-      const cplx<T> uh = x[L.f_u], vh = x[L.f_v], hh = x[L.f_h];
-      // dynamics
-      if (L.model == 0) {
-        const cplx<T> B = cadd<T>(cscale<T>(hh, (T)a.c.c2), a.ps[L.p_ke * g.ms + m]);
-        rhs[L.f_u] = csub<T>(cadd<T>(cscale<T>(vh, (T)a.c.f0), a.ps[L.p_zv * g.ms + m]), cik<T>(B, kxf));
-        rhs[L.f_v] = csub<T>(csub<T>(cscale<T>(uh, -(T)a.c.f0), a.ps[L.p_zu * g.ms + m]), cik<T>(B, kyf));
-        rhs[L.f_h] = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(a.ps[L.p_hu * g.ms + m], kxf),
-                                                   cik<T>(a.ps[L.p_hv * g.ms + m], kyf)));
-      } else {
-        const T kc = kxf * (T)a.c.adv_x + kyf * (T)a.c.adv_y;
-        rhs[L.f_u] = cik<T>(uh, -kc);
-        rhs[L.f_v] = cik<T>(vh, -kc);
-        rhs[L.f_h] = cik<T>(hh, -kc);
-      }
-      if (L.strategy > 0) {
-        // f_hat of each averaged scalar at this stage
-        cplx<T> fh[NLMF];
-        fh[LMF_ZETA] = csub<T>(cik<T>(vh, kxf), cik<T>(uh, kyf));
-        fh[LMF_H] = hh;
-        fh[LMF_U] = uh;
-        fh[LMF_V] = vh;
-        fh[LMF_Q] = L.has_q ? a.ps[L.p_q * g.ms + m] : mk<T>(0, 0);
-        for (int j = 0; j < L.nlm; ++j) {
-          const cplx<T> pg = a.ps[L.p_g[j] * g.ms + m];
-          // S1: f - u.grad g (Eq. gtilde-evol); S2: product already f(x+xi) - w.grad g
-          rhs[L.f_g[j]] = L.strategy == 1 ? csub<T>(fh[L.lmf[j]], pg) : pg;
-          if (L.eulerian) rhs[L.f_e[j]] = fh[L.lmf[j]];
-        }
-        if (L.has_pos) {
-          if (L.strategy == 1) {
-            // d_t D = s u - u.grad D
-            const T s = (T)sd;
-            cplx<T> ua = uh, va = vh;
-            if (L.model == 1) {
-              const bool k0 = (kx == 0 && kyi == g.K);
-              ua = mk<T>(k0 ? (T)a.c.adv_x : (T)0, 0);
-              va = mk<T>(k0 ? (T)a.c.adv_y : (T)0, 0);
-            }
-            rhs[L.f_p[0]] = csub<T>(cscale<T>(ua, s), a.ps[L.p_p[0] * g.ms + m]);
-            rhs[L.f_p[1]] = csub<T>(cscale<T>(va, s), a.ps[L.p_p[1] * g.ms + m]);
+      const cplx<T>* yin = a.stage == 0 ? a.y : a.ysin;
+      const int role = L.frole[f], slot = L.fslot[f];
+      cplx<T> r;
+      if (role <= R_H) {
+        // shallow-water right-hand side, Eq. (sw_eqs_dimless)
+        if (L.model == 0) {
+          if (role == R_H) {
+            r = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(a.ps[L.p_hu * g.ms + m], kxf), cik<T>(a.ps[L.p_hv * g.ms + m], kyf)));
           } else {
-            rhs[L.f_p[0]] = a.ps[L.p_p[0] * g.ms + m];
-            rhs[L.f_p[1]] = a.ps[L.p_p[1] * g.ms + m];
+            const cplx<T> hh = yin[L.f_h * g.ms + m];
+            const cplx<T> B = cadd<T>(cscale<T>(hh, (T)a.c.c2), a.ps[L.p_ke * g.ms + m]);
+            if (role == R_U)
+              r = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], (T)a.c.f0), a.ps[L.p_zv * g.ms + m]), cik<T>(B, kxf));
+            else
+              r = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -(T)a.c.f0), a.ps[L.p_zu * g.ms + m]), cik<T>(B, kyf));
           }
+        } else {
+          const T kc = kxf * (T)a.c.adv_x + kyf * (T)a.c.adv_y;
+          r = cik<T>(yin[f * g.ms + m], -kc);
+        }
+      } else if (role == R_P) {
+        const cplx<T> pp = a.ps[L.p_p[slot] * g.ms + m];
+        if (L.strategy == 1) {
+          // d_t D = s u - u.grad D
+          const T s = (T)sd;
+          cplx<T> ua;
+          if (L.model == 1) {
+            const bool k0 = (kx == 0 && kyi == g.K);
+            ua = mk<T>(k0 ? (T)(slot == 0 ? a.c.adv_x : a.c.adv_y) : (T)0, 0);
+          } else {
+            ua = yin[(slot == 0 ? L.f_u : L.f_v) * g.ms + m];
+          }
+          r = csub<T>(cscale<T>(ua, s), pp);
+        } else {
+          r = pp;  // xi: the product already holds u(x+xi) - w - w.grad xi
+        }
+      } else {
+        // f_hat of the averaged scalar at this stage
+        const int sc = L.lmf[slot];
+        cplx<T> fh;
+        if (sc == LMF_ZETA) fh = csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
+        else if (sc == LMF_H) fh = yin[L.f_h * g.ms + m];
+        else if (sc == LMF_U) fh = yin[L.f_u * g.ms + m];
+        else if (sc == LMF_V) fh = yin[L.f_v * g.ms + m];
+        else fh = a.ps[L.p_q * g.ms + m];
+        if (role == R_E) {
+          r = fh;  // Eq. (ave)
+        } else {
+          const cplx<T> pg = a.ps[L.p_g[slot] * g.ms + m];
+          // S1: f - u.grad g (Eq. gtilde-evol); S2: f(x+xi) - w.grad g
+          r = L.strategy == 1 ? csub<T>(fh, pg) : pg;
         }
       }
       // RK4 with integrating factor
-      for (int f = 0; f < L.nf; ++f) {
-        const int cls = L.fclass[f];
-        const T E = cls == IF_NONE ? (T)1 : a.ef[cls * g.ms + m];
-        const cplx<T> yn = a.y[f * g.ms + m];
-        const cplx<T> r = rhs[f];
-        const long long o = f * g.ms + m;
-        if (a.stage == 0) {
-          a.acc[o] = cscale<T>(r, E * E);
-          a.ys[o] = cscale<T>(cadd<T>(yn, cscale<T>(r, (T)0.5 * dt)), E);
-        } else if (a.stage == 1) {
-          a.acc[o] = cadd<T>(a.acc[o], cscale<T>(r, (T)2 * E));
-          a.ys[o] = cadd<T>(cscale<T>(yn, E), cscale<T>(r, (T)0.5 * dt));
-        } else if (a.stage == 2) {
-          a.acc[o] = cadd<T>(a.acc[o], cscale<T>(r, (T)2 * E));
-          a.ys[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(r, dt * E));
+      const int cls = L.fclass[f];
+      const T E = cls == IF_NONE ? (T)1 : a.ef[cls * g.ms + m];
+      const long long o = f * g.ms + m;
+      const cplx<T> yn = a.y[o];
+      if (a.stage == 0) {
+        a.acc[o] = cscale<T>(r, E * E);
+        a.ys[o] = cscale<T>(cadd<T>(yn, cscale<T>(r, (T)0.5 * dt)), E);
+      } else if (a.stage == 1) {
+        a.acc[o] = cadd<T>(a.acc[o], cscale<T>(r, (T)2 * E));
+        a.ys[o] = cadd<T>(cscale<T>(yn, E), cscale<T>(r, (T)0.5 * dt));
+      } else if (a.stage == 2) {
+        a.acc[o] = cadd<T>(a.acc[o], cscale<T>(r, (T)2 * E));
+        a.ys[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(r, dt * E));
+      } else {
+        const cplx<T> inc = cscale<T>(cadd<T>(a.acc[o], r), dt / (T)6);
+        const T E2 = E * E;
+        if (a.comp && L.fkahan[f]) {
+          cplx<T> cc = a.comp[o];
+          cc.x *= E2;
+          cc.y *= E2;
+          cplx<T> out;
+          out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
+          out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
+          a.y[o] = out;
+          a.comp[o] = cc;
         } else {
-          const cplx<T> inc = cscale<T>(cadd<T>(a.acc[o], r), dt / (T)6);
-          const T E2 = E * E;
-          if (a.comp && L.fkahan[f]) {
-            cplx<T> cc = a.comp[o];
-            cc.x *= E2;
-            cc.y *= E2;
-            cplx<T> out;
-            out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
-            out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
-            a.y[o] = out;
-            a.comp[o] = cc;
-          } else {
-            a.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
-          }
+          a.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
         }
       }
     }
@@ -580,7 +602,7 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ UpdateAr
     if (threadIdx.x == 0) {
       __threadfence();
       const unsigned t = atomicAdd(a.ticket, 1u);
-      if (t == gridDim.x - 1) {
+      if (t == gridDim.x * gridDim.y - 1) {
         *a.ticket = 0u;
         *a.ctr = *a.ctr + 1;
         __threadfence();

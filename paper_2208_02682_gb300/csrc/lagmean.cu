@@ -32,7 +32,7 @@ struct sw_handle {
   // device memory
   void* arena = nullptr;
   size_t arena_bytes = 0;
-  void *y = nullptr, *ys = nullptr, *acc = nullptr, *comp = nullptr, *ps = nullptr;
+  void *y = nullptr, *ys = nullptr, *ys2 = nullptr, *acc = nullptr, *comp = nullptr, *ps = nullptr;
   void *mix = nullptr, *pmix = nullptr, *phys = nullptr, *ef = nullptr, *tw = nullptr;
   double2 *tw64 = nullptr, *spec64 = nullptr, *mix64 = nullptr;
   double *out64 = nullptr, *part = nullptr, *dres = nullptr;
@@ -45,9 +45,14 @@ struct sw_handle {
   int64_t done = 0;
   int64_t steps_total = 0;
   Layout L{};
-  // captured single-step graph for the current layout
+  // captured graphs of 1 and GRAPH_STEPS RK4 steps for the current layout
   cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec_multi = nullptr;
   bool graph_valid = false;
+  int64_t kernels_per_step = 0;
+  int64_t launches = 0;  // kernels launched since creation
+  // launch shape of the row pass (rows per block, product pairs per block)
+  int rows_prod = 1, ppb = 1, rows_inv = 1;
 };
 
 static int fail(sw_handle* h, int code, const std::string& msg) {
@@ -81,6 +86,8 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
   for (int f = 0; f < 3; ++f) {
     L.fclass[f] = IF_DYN;
     L.fkahan[f] = 0;
+    L.frole[f] = R_U + f;
+    L.fslot[f] = 0;
   }
   if (strategy > 0) {
     const int bits[NLMF] = {LM_ZETA, LM_H, LM_U, LM_V, LM_Q};
@@ -89,23 +96,18 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
     L.has_q = (fields & LM_Q) ? 1 : 0;
     L.has_pos = (strategy == 2 || (fields & LM_POS)) ? 1 : 0;
     L.eulerian = eulerian ? 1 : 0;
-    for (int j = 0; j < L.nlm; ++j) {
-      L.f_g[j] = nf;
-      L.fclass[nf] = IF_LM;
-      L.fkahan[nf++] = 1;
-    }
+    auto addf = [&](int cls, int role, int slot) {
+      L.fclass[nf] = cls;
+      L.fkahan[nf] = 1;
+      L.frole[nf] = role;
+      L.fslot[nf] = slot;
+      return nf++;
+    };
+    for (int j = 0; j < L.nlm; ++j) L.f_g[j] = addf(IF_LM, R_G, j);
     if (L.has_pos)
-      for (int c = 0; c < 2; ++c) {
-        L.f_p[c] = nf;
-        L.fclass[nf] = IF_LM;
-        L.fkahan[nf++] = 1;
-      }
+      for (int c = 0; c < 2; ++c) L.f_p[c] = addf(IF_LM, R_P, c);
     if (L.eulerian)
-      for (int j = 0; j < L.nlm; ++j) {
-        L.f_e[j] = nf;
-        L.fclass[nf] = IF_NONE;
-        L.fkahan[nf++] = 1;
-      }
+      for (int j = 0; j < L.nlm; ++j) L.f_e[j] = addf(IF_NONE, R_E, j);
   }
   L.nf = nf;
   // column-pass outputs
@@ -166,17 +168,90 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
 }
 
 // ---------------------------------------------------------------------------
+// Algorithmic bytes of one launch of each stepping kernel: the distinct input
+// elements it must read and the output elements it must write (box modes
+// NY*KX, mixed rows N*KX, physical N*N), not counting L2 hits or padding.
+struct KBytes {
+  double col_inv, row_inv, phys_q, row_prod, col_fwd, update[4];
+};
+
+static KBytes kernel_bytes(const sw_handle* h, const Layout& L) {
+  const Geom& g = h->g;
+  const double cs = 2.0 * h->tsz, ts = (double)h->tsz;
+  const double MB = (double)g.NY * g.KX, MI = (double)g.N * g.KX, NP = (double)g.np;
+  KBytes b;
+  bool seen[MAXF] = {};
+  int nsrc = 0;
+  for (int i = 0; i < L.ni; ++i) {
+    if (!seen[L.i_src[i]]) { seen[L.i_src[i]] = true; ++nsrc; }
+    if (L.i_src2[i] >= 0 && !seen[L.i_src2[i]]) { seen[L.i_src2[i]] = true; ++nsrc; }
+  }
+  b.col_inv = nsrc * MB * cs + L.ni * MI * cs;
+  b.row_inv = 4 * MI * cs + 4 * NP * ts;
+  b.phys_q = 3 * NP * ts;
+  double rp = L.np * MI * cs;
+  if (L.strategy == 2) {
+    bool gat[NPH] = {};
+    int ng = 0;
+    for (int p = 0; p < L.np; ++p) {
+      int f = -1;
+      if (L.pk[p] == PK_XI && L.model == 0) f = L.pc[p];
+      if (L.pk[p] == PK_GBAR) f = L.pc[p];
+      if (f >= 0 && !gat[f]) { gat[f] = true; ++ng; }
+    }
+    rp += (L.ni - 4) * MI * cs + 4 * NP * ts + ng * NP * ts;
+  } else {
+    rp += L.ni * MI * cs;
+  }
+  b.row_prod = rp;
+  b.col_fwd = L.np * (MI + MB) * cs;
+  int nk = 0;
+  for (int f = 0; f < L.nf; ++f) nk += L.fkahan[f];
+  const double nf = L.nf, np = L.np;
+  b.update[0] = (nf + np + 2 * nf) * MB * cs + 2 * MB * ts;
+  b.update[1] = b.update[2] = (3 * nf + np + 2 * nf) * MB * cs + 2 * MB * ts;
+  b.update[3] = (3 * nf + np + nf + (h->fp32 ? 2 * nk : 0)) * MB * cs + 2 * MB * ts;
+  return b;
+}
+
+// Optional per-launch event bracketing (sw_kernel_times).
+struct Prof {
+  enum { MAXEV = 64 };
+  cudaEvent_t ev[2 * MAXEV];
+  int cls[MAXEV];
+  double bytes[MAXEV];
+  int n = 0;
+};
+
+#define LAUNCH(cls_, bytes_, ...)                                    \
+  do {                                                               \
+    if (pf) cudaEventRecord(pf->ev[2 * pf->n], s);                   \
+    if ((e = (__VA_ARGS__)) != cudaSuccess) return e;                \
+    if (pf) {                                                        \
+      cudaEventRecord(pf->ev[2 * pf->n + 1], s);                     \
+      pf->cls[pf->n] = (cls_);                                       \
+      pf->bytes[pf->n] = (bytes_);                                   \
+      pf->n++;                                                       \
+    }                                                                \
+    ++*nlaunch;                                                      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
 // Stage pipeline (one RK4 step = 4 stages) for precision T.
 template <typename T>
-static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
+static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s, Prof* pf, int64_t* nlaunch) {
   const Layout& L = h->L;
   const Geom& g = h->g;
+  const KBytes kb = kernel_bytes(h, L);
   cplx<T>* y = (cplx<T>*)h->y;
-  cplx<T>* ys = (cplx<T>*)h->ys;
+  // stage inputs: stage 1 and 3 read ysa, stage 2 reads ysb
+  cplx<T>* ysa = (cplx<T>*)h->ys;
+  cplx<T>* ysb = (cplx<T>*)h->ys2;
   StepConsts c{h->p.dt, h->p.f0, h->p.c2, h->p.adv_x, h->p.adv_y};
   cudaError_t e;
   for (int stage = 0; stage < 4; ++stage) {
-    const cplx<T>* src = stage == 0 ? y : ys;
+    const cplx<T>* src = stage == 0 ? y : (stage == 2 ? ysb : ysa);
+    cplx<T>* dst_next = (stage == 1) ? ysb : ysa;
     if (L.np > 0) {
       ColInvArgs<T> ci;
       ci.src = src;
@@ -190,8 +265,7 @@ static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
         ci.op[i] = L.i_op[i];
         ci.dst_idx[i] = i;
       }
-      if ((e = launch_col_inv<T>(ci, s)) != cudaSuccess) return e;
-      const int B = row_block_rows(g.N);
+      LAUNCH(SW_K_COL_INV, kb.col_inv, launch_col_inv<T>(ci, s));
       if (L.strategy == 2) {
         RowInvArgs<T, T> ri;
         std::memset(&ri, 0, sizeof(ri));
@@ -200,13 +274,13 @@ static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
         ri.dst_stride = g.np;
         ri.tw = (const cplx<T>*)h->tw;
         ri.g = g;
-        ri.B = B;
+        ri.B = h->rows_inv;
         ri.npairs = 2;
         ri.a_idx[0] = L.i_u; ri.b_idx[0] = L.i_v; ri.oa[0] = PH_U; ri.ob[0] = PH_V;
         ri.a_idx[1] = L.i_h; ri.b_idx[1] = L.i_z; ri.oa[1] = PH_H; ri.ob[1] = PH_Z;
         for (int p = 0; p < 2; ++p) ri.sa[p] = ri.sb[p] = 1.0;
-        if ((e = launch_row_inv<T, T>(ri, s)) != cudaSuccess) return e;
-        if (L.has_q && (e = launch_phys_q<T>((T*)h->phys, g.np, h->p.f0, s)) != cudaSuccess) return e;
+        LAUNCH(SW_K_ROW_INV, kb.row_inv, launch_row_inv<T, T>(ri, s));
+        if (L.has_q) LAUNCH(SW_K_PHYS_Q, kb.phys_q, launch_phys_q<T>((T*)h->phys, g.np, h->p.f0, s));
       }
       RowProdArgs<T> rp;
       rp.mix = (const cplx<T>*)h->mix;
@@ -217,9 +291,10 @@ static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
       rp.g = g;
       rp.L = L;
       rp.c = c;
-      rp.B = B;
+      rp.B = h->rows_prod;
+      rp.ppb = h->ppb;
       rp.stage = stage;
-      if ((e = launch_row_prod<T>(rp, s)) != cudaSuccess) return e;
+      LAUNCH(SW_K_ROW_PROD, kb.row_prod, launch_row_prod<T>(rp, s));
       ColFwdArgs<T> cf;
       cf.src = (const cplx<T>*)h->pmix;
       cf.dst = (cplx<T>*)h->ps;
@@ -227,11 +302,12 @@ static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
       cf.g = g;
       cf.nout = L.np;
       for (int i = 0; i < L.np; ++i) cf.src_idx[i] = cf.dst_idx[i] = i;
-      if ((e = launch_col_fwd<T>(cf, s)) != cudaSuccess) return e;
+      LAUNCH(SW_K_COL_FWD, kb.col_fwd, launch_col_fwd<T>(cf, s));
     }
     UpdateArgs<T> ua;
     ua.y = y;
-    ua.ys = ys;
+    ua.ysin = src;
+    ua.ys = dst_next;
     ua.acc = (cplx<T>*)h->acc;
     ua.comp = h->fp32 ? (cplx<T>*)h->comp : nullptr;
     ua.ps = (const cplx<T>*)h->ps;
@@ -242,38 +318,56 @@ static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s) {
     ua.L = L;
     ua.c = c;
     ua.stage = stage;
-    if ((e = launch_update<T>(ua, s)) != cudaSuccess) return e;
+    LAUNCH(SW_K_UPDATE, kb.update[stage], launch_update<T>(ua, s));
   }
   return cudaSuccess;
 }
 
+static const int GRAPH_STEPS = 8;
+
 static void drop_graph(sw_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
+  if (h->gexec_multi) cudaGraphExecDestroy(h->gexec_multi);
+  h->gexec = h->gexec_multi = nullptr;
   h->graph_valid = false;
 }
 
-static int ensure_graph(sw_handle* h) {
-  if (h->graph_valid) return SW_OK;
-  drop_graph(h);
-  // capture on a private stream (the caller's stream may be the legacy
-  // default stream, which cannot be captured); the graph is launched on the
-  // caller's stream
+// Capture `steps` RK4 steps into an executable graph.  Capture runs on a
+// private stream (the caller's stream may be the legacy default stream, which
+// cannot be captured); the graphs are launched on the caller's stream.
+static int capture_steps(sw_handle* h, int steps, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = h->fp32 ? enqueue_step<float>(h, h->cap_stream) : enqueue_step<double>(h, h->cap_stream);
+  int64_t nl = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < steps && e == cudaSuccess; ++i)
+    e = h->fp32 ? enqueue_step<float>(h, h->cap_stream, nullptr, &nl)
+                : enqueue_step<double>(h, h->cap_stream, nullptr, &nl);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
   if (e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return fail_cuda(h, "enqueue_step (capture)", e);
   }
   if (e2 != cudaSuccess) return fail_cuda(h, "cudaStreamEndCapture", e2);
-  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    h->gexec = nullptr;
+    *out = nullptr;
     return fail_cuda(h, "cudaGraphInstantiate", e);
+  }
+  h->kernels_per_step = nl / steps;
+  return SW_OK;
+}
+
+static int ensure_graph(sw_handle* h) {
+  if (h->graph_valid) return SW_OK;
+  drop_graph(h);
+  int rc = capture_steps(h, 1, &h->gexec);
+  if (rc == SW_OK) rc = capture_steps(h, GRAPH_STEPS, &h->gexec_multi);
+  if (rc != SW_OK) {
+    drop_graph(h);
+    return rc;
   }
   h->graph_valid = true;
   return SW_OK;
@@ -283,8 +377,11 @@ static int run_steps(sw_handle* h, int64_t n) {
   if (n <= 0) return SW_OK;
   int rc = ensure_graph(h);
   if (rc) return rc;
-  for (int64_t i = 0; i < n; ++i) CK(h, cudaGraphLaunch(h->gexec, h->stream));
+  int64_t i = 0;
+  for (; i + GRAPH_STEPS <= n; i += GRAPH_STEPS) CK(h, cudaGraphLaunch(h->gexec_multi, h->stream));
+  for (; i < n; ++i) CK(h, cudaGraphLaunch(h->gexec, h->stream));
   h->steps_total += n;
+  h->launches += n * h->kernels_per_step;
   return SW_OK;
 }
 
@@ -329,7 +426,7 @@ static int spectral_pair_to_phys(sw_handle* h, const OutSpec& a, const OutSpec* 
   ri.dst_stride = g.np;
   ri.tw = h->tw64;
   ri.g = g;
-  ri.B = row_block_rows(g.N);
+  ri.B = h->rows_inv;
   ri.npairs = 1;
   ri.a_idx[0] = 0;
   ri.b_idx[0] = b ? 1 : -1;
@@ -344,6 +441,7 @@ static int spectral_pair_to_phys(sw_handle* h, const OutSpec& a, const OutSpec* 
     ri.ayb[0] = b->ay;
   }
   CK(h, launch_row_inv<double, double>(ri, s));
+  h->launches += 3;
   return SW_OK;
 }
 
@@ -366,7 +464,7 @@ static int load_ic_from_out64(sw_handle* h) {
   rf.dst = h->mix64;
   rf.tw = h->tw64;
   rf.g = g;
-  rf.B = row_block_rows(g.N);
+  rf.B = h->rows_inv;
   rf.npairs = 2;
   rf.a_idx[0] = 0; rf.b_idx[0] = 1; rf.oa[0] = 0; rf.ob[0] = 1;
   rf.a_idx[1] = 2; rf.b_idx[1] = -1; rf.oa[1] = 2; rf.ob[1] = -1;
@@ -381,6 +479,7 @@ static int load_ic_from_out64(sw_handle* h) {
   CK(h, launch_col_fwd<double>(cf, s));
   if (h->fp32) CK(h, launch_spec_from_f64<float>(h->spec64, (cplx<float>*)h->y, 3 * g.ms, s));
   else CK(h, launch_spec_from_f64<double>(h->spec64, (cplx<double>*)h->y, 3 * g.ms, s));
+  h->launches += 3;
   return SW_OK;
 }
 
@@ -465,10 +564,14 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   g.np = (long long)g.N * g.N;
   const size_t cs = 2 * h->tsz;  // complex T
   h->diag_blocks = 1024;
+  h->rows_prod = row_block_rows(g.N);
+  h->rows_inv = row_block_rows(g.N);
+  h->ppb = g.N <= 512 ? 1 : MAXP;
   // arena layout
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-  const size_t o_y = take(MAXF * g.ms * cs), o_ys = take(MAXF * g.ms * cs), o_acc = take(MAXF * g.ms * cs);
+  const size_t o_y = take(MAXF * g.ms * cs), o_ys = take(MAXF * g.ms * cs), o_ys2 = take(MAXF * g.ms * cs);
+  const size_t o_acc = take(MAXF * g.ms * cs);
   const size_t o_comp = take(MAXF * g.ms * cs), o_ps = take(MAXP * g.ms * cs);
   const size_t o_mix = take(MAXI * g.mi * cs), o_pmix = take(MAXP * g.mi * cs);
   const size_t o_phys = take(NPH * g.np * h->tsz), o_ef = take(2 * g.ms * h->tsz), o_tw = take(g.N * cs);
@@ -484,7 +587,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
     return fail(nullptr, SW_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
   char* base = (char*)h->arena;
-  h->y = base + o_y; h->ys = base + o_ys; h->acc = base + o_acc; h->comp = base + o_comp; h->ps = base + o_ps;
+  h->y = base + o_y; h->ys = base + o_ys; h->ys2 = base + o_ys2; h->acc = base + o_acc; h->comp = base + o_comp; h->ps = base + o_ps;
   h->mix = base + o_mix; h->pmix = base + o_pmix; h->phys = base + o_phys; h->ef = base + o_ef;
   h->tw = base + o_tw; h->tw64 = (double2*)(base + o_tw64); h->spec64 = (double2*)(base + o_spec64);
   h->mix64 = (double2*)(base + o_mix64); h->out64 = (double*)(base + o_out64);
@@ -648,7 +751,7 @@ extern "C" int lmean_end(sw_handle* h, const lm_result* out) {
   if (rc) return rc;
   for (int i = 0; i < n; ++i)
     if ((rc = copy_out(h, dst[i], i, out->on_device))) return rc;
-  CK(h, cudaStreamSynchronize(h->stream));
+  if (!out->on_device) CK(h, cudaStreamSynchronize(h->stream));
   h->lm_open = false;
   drop_graph(h);
   h->L = build_layout(h->p.model, 0, 0, 0);
@@ -714,7 +817,7 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   ri.dst_stride = g.np;
   ri.tw = h->tw64;
   ri.g = g;
-  ri.B = row_block_rows(g.N);
+  ri.B = h->rows_inv;
   ri.npairs = 1;
   ri.a_idx[0] = 0;
   ri.b_idx[0] = -1;
@@ -723,6 +826,7 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   ri.sa[0] = 1.0;
   CK(h, launch_row_inv<double, double>(ri, h->stream));
   CK(h, launch_diag(h->out64, g.np, h->p.f0, h->p.c2, h->part, h->diag_blocks, h->dres, h->stream));
+  h->launches += 5;
   double res[4] = {0, 0, 0, 0};
   CK(h, cudaMemcpyAsync(res, h->dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   // mass: the k = 0 coefficient of h (row ky = 0, column kx = 0)
@@ -812,6 +916,58 @@ extern "C" int sw_set_state(sw_handle* h, const void* blob, size_t size) {
   h->lp = hd.lp;
   h->done = hd.done;
   h->steps_total = hd.steps_total;
+  return SW_OK;
+}
+
+extern "C" int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUNT], int64_t launches[SW_K_COUNT],
+                               double bytes[SW_K_COUNT]) {
+  if (!h) return SW_EINVAL;
+  h->err.clear();
+  if (!ms || !launches || !bytes) return fail(h, SW_EINVAL, "output arrays are NULL");
+  if (nsteps < 1) return fail(h, SW_EINVAL, "nsteps must be >= 1");
+  if (h->lm_open && nsteps > h->lp.n_steps - h->done) return fail(h, SW_ERANGE, "more steps than remain in the interval");
+  for (int k = 0; k < SW_K_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    bytes[k] = 0.0;
+  }
+  Prof pf;
+  int nev = 0;
+  cudaError_t e = cudaSuccess;
+  for (; nev < 2 * Prof::MAXEV; ++nev)
+    if ((e = cudaEventCreate(&pf.ev[nev])) != cudaSuccess) break;
+  int rc = SW_OK;
+  if (e != cudaSuccess) rc = fail_cuda(h, "cudaEventCreate", e);
+  for (int64_t it = 0; rc == SW_OK && it < nsteps; ++it) {
+    pf.n = 0;
+    int64_t nl = 0;
+    e = h->fp32 ? enqueue_step<float>(h, h->stream, &pf, &nl) : enqueue_step<double>(h, h->stream, &pf, &nl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      rc = fail_cuda(h, "sw_kernel_times step", e);
+      break;
+    }
+    h->launches += nl;
+    h->steps_total += 1;
+    if (h->lm_open) h->done += 1;
+    for (int i = 0; i < pf.n; ++i) {
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, pf.ev[2 * i], pf.ev[2 * i + 1])) != cudaSuccess) {
+        rc = fail_cuda(h, "cudaEventElapsedTime", e);
+        break;
+      }
+      ms[pf.cls[i]] += t;
+      launches[pf.cls[i]] += 1;
+      bytes[pf.cls[i]] += pf.bytes[i];
+    }
+  }
+  for (int i = 0; i < nev; ++i) cudaEventDestroy(pf.ev[i]);
+  return rc;
+}
+
+extern "C" int sw_launch_count(sw_handle* h, int64_t* count) {
+  if (!h || !count) return SW_EINVAL;
+  *count = h->launches;
   return SW_OK;
 }
 

@@ -5,18 +5,18 @@
 
 namespace lm {
 
-// threads and rows per block of the row kernels: B rows of N points with
-// B*N/8 threads (one 8-element Stockham butterfly set per thread and pass)
-inline int row_block_rows(int N) {
-  int B = 2048 / N;
+// Rows per block of the row kernels: B rows of N points run with B*N/8
+// threads (one 8-element Stockham butterfly set per thread and pass).
+// `points` = B*N; 512 keeps small grids spread over many SMs.
+inline int row_block_rows(int N, int points = 512) {
+  int B = points / N;
   if (B > N) B = N;
   if (B < 1) B = 1;
   return B;
 }
 
-template <typename T> size_t row_prod_smem(const Geom& g, int strategy) {
-  const int B = row_block_rows(g.N);
-  return (size_t)2 * B * pad8(g.N) * sizeof(cplx<T>) + (size_t)(strategy == 2 ? 6 : 4) * B * g.N * sizeof(T);
+template <typename T> size_t row_prod_smem(int N, int B, int strategy) {
+  return (size_t)2 * B * pad8(N) * sizeof(cplx<T>) + (size_t)(strategy == 2 ? 6 : 4) * B * N * sizeof(T);
 }
 
 template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStream_t s);
@@ -77,15 +77,17 @@ template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStr
 }
 
 template <typename T> cudaError_t launch_row_prod(const RowProdArgs<T>& a, cudaStream_t s) {
-  const size_t sm = row_prod_smem<T>(a.g, a.L.strategy);
-  k_row_prod<T><<<a.g.N / a.B, a.B * a.g.N / 8, sm, s>>>(a);
+  const size_t sm = row_prod_smem<T>(a.g.N, a.B, a.L.strategy);
+  const int npairs = (a.L.np + 1) / 2;
+  dim3 grid(a.g.N / a.B, (npairs + a.ppb - 1) / a.ppb);
+  k_row_prod<T><<<grid, a.B * a.g.N / 8, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T> cudaError_t launch_update(const UpdateArgs<T>& a, cudaStream_t s) {
   const int thr = 256;
   const long long nb = (a.g.ms + thr - 1) / thr;
-  k_update<T><<<(unsigned)nb, thr, 0, s>>>(a);
+  k_update<T><<<dim3((unsigned)nb, a.L.nf), thr, 0, s>>>(a);
   return cudaGetLastError();
 }
 
