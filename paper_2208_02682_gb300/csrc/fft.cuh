@@ -52,12 +52,34 @@ __device__ __forceinline__ void dft8(cplx<T>* v) {
   v[3] = cadd<T>(a3, b3); v[7] = csub<T>(a3, b3);
 }
 
+// Twiddles w^{r k}, r < R, of one butterfly from at most three table loads
+// (w^k, w^2k, w^4k); the others are products of those (at most two
+// multiplications deep).
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int tstep, const cplx<T>* __restrict__ tw) {
+  auto ld = [&](int e) {
+    cplx<T> t = __ldg(&tw[e << tstep]);
+    if (SIGN > 0) t.y = -t.y;
+    return t;
+  };
+  w[1] = ld(k);
+  if (R >= 4) {
+    w[2] = ld(2 * k);
+    w[3] = cmul<T>(w[1], w[2]);
+  }
+  if (R == 8) {
+    w[4] = ld(4 * k);
+    w[5] = cmul<T>(w[4], w[1]);
+    w[6] = cmul<T>(w[4], w[2]);
+    w[7] = cmul<T>(w[4], w[3]);
+  }
+}
+
 template <typename T, int SIGN, int LR>
 __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, int bstride,
                                               const cplx<T>* __restrict__ tw) {
   constexpr int R = 1 << LR;
   constexpr int NB = 8 / R;  // butterflies per thread
-  const int N = 1 << log2N;
   const int lNR = log2N - LR;
   const int NR = 1 << lNR;
   const int Ns = 1 << lNs;
@@ -71,21 +93,18 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
     const int b = g >> lNR;
     const int j = g & (NR - 1);
     const int k = j & (Ns - 1);
-    cplx<T>* src = buf + b * bstride;
+    const cplx<T>* src = buf + b * bstride;
     base[u] = b * bstride;
     outb[u] = ((j - k) << LR) + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      cplx<T> x = src[pad8(j + r * NR)];
-      if (r > 0 && k > 0) {
-        cplx<T> w = __ldg(&tw[(r * k) << tstep]);
-        if (SIGN > 0) w.y = -w.y;
-        x = cmul<T>(x, w);
-      }
-      v[u * R + r] = x;
+    for (int r = 0; r < R; ++r) v[u * R + r] = src[pad8(j + r * NR)];
+    if (k > 0) {
+      cplx<T> w[R];
+      butterfly_twiddles<T, SIGN, R>(w, k, tstep, tw);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], w[r]);
     }
   }
-  (void)N;
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < NB; ++u) {

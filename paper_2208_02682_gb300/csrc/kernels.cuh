@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
     row_pair_inverse<T>(W, a.mix + (long long)L.i_xi[0] * g.mi, a.mix + (long long)L.i_xi[1] * g.mi,
                         row0, B, g, a.tw);
     for (int e = tid; e < BN; e += nthr) {
-      const int r = e / N, x = e - r * N;
+      const int r = e >> g.log2N, x = e & (N - 1);
       const cplx<T> v = W[r * bst + pad8(x)];
       XI[e] = v.x;
       XI[BN + e] = v.y;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
       row_pair_inverse<T>(W, a.mix + (long long)L.i_u * g.mi, a.mix + (long long)L.i_v * g.mi, row0, B, g,
                           a.tw);
       for (int e = tid; e < BN; e += nthr) {
-        const int r = e / N, x = e - r * N;
+        const int r = e >> g.log2N, x = e & (N - 1);
         const cplx<T> v = W[r * bst + pad8(x)];
         U[e] = v.x;
         U[BN + e] = v.y;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
       row_pair_inverse<T>(W, a.mix + (long long)L.i_h * g.mi, a.mix + (long long)L.i_z * g.mi, row0, B, g,
                           a.tw);
       for (int e = tid; e < BN; e += nthr) {
-        const int r = e / N, x = e - r * N;
+        const int r = e >> g.log2N, x = e & (N - 1);
         const cplx<T> v = W[r * bst + pad8(x)];
         U[2 * BN + e] = v.x;
         U[3 * BN + e] = v.y;
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256) k_row_prod(const __grid_constant__ RowPro
                           g, a.tw);
     }
     for (int e = tid; e < BN; e += nthr) {
-      const int r = e / N, x = e - r * N;
+      const int r = e >> g.log2N, x = e & (N - 1);
       const T u = U[e], v = U[BN + e], h = U[2 * BN + e], z = U[3 * BN + e];
       T val;
       switch (kind) {

@@ -1,0 +1,76 @@
+"""Run one configuration for a few RK4 steps and print per-kernel device times.
+
+Used for profiling captures and quick timings of a single grid:
+
+  python -m paper_2208_02682_gb300.runcase --N 2048 --strategy 1 --precision f32 --steps 4
+
+It creates one handle from the seeded turbulence-plus-wave initial condition,
+opens an averaging interval, replays `--graph-steps` steps from the captured
+graph (timed with CUDA events), then launches `--steps` steps kernel by
+kernel through sw_kernel_times and prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--strategy", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--graph-steps", type=int, default=16)
+    ap.add_argument("--fields", default="zeta,h,u,v")
+    ap.add_argument("--seed", type=int, default=1003)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import paper_2208_02682_gb300 as lm
+    import sw_inputs as si
+
+    lm.build()
+    N = args.N
+    K = (N - 1) // 3
+    dt = 5e-3 if N <= 1024 else 2.5e-3
+    ic = np.ascontiguousarray(np.stack(si.turbulence_plus_waves(N, 0.05, 2.0, 8.0, 12.0, args.seed)))
+    h = lm.sw_create(lm.make_params(N, dt, precision=args.precision, nu8=10.0 / K ** 8), ic)
+    fields = tuple(f for f in args.fields.split(",") if f)
+    total = args.graph_steps + args.steps
+    if args.strategy:
+        lm.lmean_begin(h, lm.make_lm_params(args.strategy, fields, n_steps=total))
+    step = (lambda n: lm.lmean_step(h, n)) if args.strategy else (lambda n: lm.sw_step(h, n))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step(args.graph_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / max(1, args.graph_steps)
+    kt = lm.sw_kernel_times(h, args.steps)
+    lm.sw_destroy(h)
+    tot = sum(v[0] for v in kt.values())
+    out = {
+        "N": N, "strategy": args.strategy, "precision": args.precision, "fields": list(fields),
+        "graph_ms_per_step": graph_ms,
+        "gp_steps_per_s": N * N / (graph_ms * 1e-3),
+        "kernels": {k: {"ms_per_launch": t / c, "launches": c, "share": t / tot,
+                        "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9}
+                    for k, (t, c, b) in sorted(kt.items(), key=lambda kv: -kv[1][0])},
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
