@@ -201,11 +201,42 @@ int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUNT],
  * replays count each kernel node). */
 int sw_launch_count(sw_handle* h, int64_t* count);
 
+/* ---- allocation-free projection --------------------------------------------
+ * The paper has no counterpart to this call; it is a library convenience.
+ * Some callers cannot allocate device memory: code running where a
+ * framework's caching allocator owns the GPU memory and no other allocation
+ * is allowed, or latency-critical loops in which cudaMalloc/cudaFree (which
+ * may synchronise the device) are not acceptable.  sw_project_static serves
+ * them: it projects one physical field onto the 2/3-dealiased spectral box
+ * (forward 2D FFT, keep |kx|, |ky| <= floor((N-1)/3), inverse 2D FFT), in
+ * FP64, the same operation as sw_create followed by sw_get_fields, and it
+ * allocates nothing.  Its scratch (mixed and spectral intermediates and the
+ * twiddle table) is a file-scope static device array of
+ * SW_PROJECT_STATIC_BYTES bytes that every GPU loading the library holds
+ * until the process exits.
+ *   in, out: device pointers to N*N doubles (row-major, y slow); they may
+ *            be the same buffer.  The caller owns both.
+ *   N:       power of two in [16, SW_PROJECT_STATIC_MAX_N]; larger N is
+ *            rejected with SW_EINVAL (message via sw_last_error(NULL)).
+ *   stream:  cudaStream_t (NULL: legacy default stream); the call is
+ *            asynchronous on it.
+ * The first call on a device resolves the device address of the static
+ * array (cudaGetSymbolAddress) and sets kernel attributes, once per device;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array, which keeps the last call's contents (each call
+ * overwrites all it reads), so calls that overlap on the GPU (different
+ * streams, or host threads) race and must be serialised by the caller.
+ * Errors: SW_EINVAL, SW_ECUDA. */
+#define SW_PROJECT_STATIC_MAX_N 512
+#define SW_PROJECT_STATIC_BYTES (3u << 20)
+int sw_project_static(const double* in, double* out, int N, void* stream);
+
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);
 
 /* Message for the last failing call on h ("" if none); valid until the next
- * call on h.  With h == NULL, the message of the last failing sw_create. */
+ * call on h.  With h == NULL, the message of the last failing sw_create or
+ * sw_project_static on the calling thread. */
 const char* sw_last_error(sw_handle* h);
 
 /* Library version string. */

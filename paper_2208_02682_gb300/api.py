@@ -26,7 +26,7 @@ FIELD_BITS = {"zeta": LM_ZETA, "h": LM_H, "u": LM_U, "v": LM_V, "q": LM_Q}
 EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "lmean_end",
            "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
            "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version", "sw_kernel_times",
-           "sw_launch_count")
+           "sw_launch_count", "sw_project_static")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "sw_last_error": (C.c_char_p, [H]),
         "sw_kernel_times": (C.c_int, [H, C.c_int64, _DP, C.POINTER(C.c_int64), _DP]),
         "sw_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
+        "sw_project_static": (C.c_int, [_DP, _DP, C.c_int, C.c_void_p]),
         "sw_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -258,6 +259,20 @@ def sw_launch_count(h):
     n = C.c_int64()
     _check(load().sw_launch_count(h, C.byref(n)), h)
     return n.value
+
+
+def sw_project_static(inp, out, N, stream=None):
+    """Allocation-free projection of a device field onto the dealiased box
+    (see include/lagmean.h); inp, out: contiguous float64 CUDA tensors."""
+    pi, di = _ptr(inp)
+    po, do = _ptr(out)
+    if not (di and do):
+        raise ValueError("sw_project_static takes device tensors")
+    lib = load()
+    rc = lib.sw_project_static(pi, po, int(N), C.c_void_p(stream or 0))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return out
 
 
 def sw_last_error(h=None):

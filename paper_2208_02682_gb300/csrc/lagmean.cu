@@ -21,6 +21,11 @@ cudaError_t prepare_kernels_f64();
 
 static thread_local std::string g_create_error;
 
+namespace lm {
+// message for calls without a handle (sw_create, sw_project_static)
+void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace lm
+
 struct sw_handle {
   sw_params p;
   Geom g;
