@@ -201,6 +201,47 @@ int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUNT],
  * replays count each kernel node). */
 int sw_launch_count(sw_handle* h, int64_t* count);
 
+/* ---- batches: many runs in the same launches ---------------------------------
+ * A batch steps several handles together: every kernel of an RK stage is one
+ * launch over all members (a device table of per-run descriptors maps each
+ * block to its run), and the steps replay from captured CUDA graphs.  Members
+ * may differ in grid size, strategy, field set and interval state; each
+ * member's arithmetic is the same as when it steps alone, so its results are
+ * bit-for-bit the same alone and in the batch.  A batch does not own its
+ * members: destroy the batch before any member.  Members must share the
+ * precision and the stream they were created with; grids of different sizes
+ * must all lie in 64..512 (larger grids batch only with their own size).
+ * Calls on member handles (lmean_begin, lmean_end, sw_get_fields, ...)
+ * remain valid between batch steps; the batch re-reads changed members
+ * before its next step. */
+typedef struct sw_batch sw_batch;
+
+/* Errors: SW_EINVAL (empty, NULL or repeated handle, mixed precision or
+ * stream, incompatible block shapes), SW_ENOMEM, SW_ECUDA.  The message of
+ * a failing create is given by sw_last_error(NULL). */
+int sw_batch_create(sw_handle* const* handles, int n, sw_batch** out);
+
+/* Advance every member by nsteps >= 0 RK4 steps (its dynamics, and its open
+ * interval if it has one).  SW_ERANGE if nsteps exceeds the steps remaining
+ * in a member's open interval (nothing is stepped then).  Asynchronous. */
+int sw_batch_step(sw_batch* b, int64_t nsteps);
+
+/* Autotuner: times the row-pass launch shapes (points per block 512, 1024 or
+ * 2048; product pairs per block 1, 2, 3 or all) on trial_steps >= 1 replayed
+ * steps each, keeps the fastest for all members and returns its index in
+ * *choice (may be NULL).  The members' states are saved before the trials and
+ * restored after them (temporary device copies).  Synchronises. */
+int sw_batch_tune(sw_batch* b, int trial_steps, int* choice);
+
+/* Kernels launched by the batch since its creation. */
+int sw_batch_launch_count(sw_batch* b, int64_t* count);
+
+/* Message for the last failing call on b. */
+const char* sw_batch_last_error(sw_batch* b);
+
+/* Release the batch (not its members; synchronises).  NULL: no-op. */
+void sw_batch_destroy(sw_batch* b);
+
 /* ---- allocation-free projection --------------------------------------------
  * The paper has no counterpart to this call; it is a library convenience.
  * Some callers cannot allocate device memory: code running where a

@@ -10,5 +10,6 @@ from .api import (  # noqa: F401
     SWError, make_params, make_lm_params, sw_create, sw_destroy, sw_step, lmean_begin,
     lmean_step, lmean_end, lmean_progress, sw_get_fields, sw_set_fields, sw_diag,
     sw_get_state, sw_set_state, sw_time, sw_sync, sw_last_error, sw_version, sw_kernel_times,
-    sw_launch_count, sw_project_static,
+    sw_launch_count, sw_project_static, sw_batch_create, sw_batch_step, sw_batch_tune,
+    sw_batch_launch_count, sw_batch_last_error, sw_batch_destroy,
 )

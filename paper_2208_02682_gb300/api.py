@@ -26,7 +26,8 @@ FIELD_BITS = {"zeta": LM_ZETA, "h": LM_H, "u": LM_U, "v": LM_V, "q": LM_Q}
 EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "lmean_end",
            "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
            "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version", "sw_kernel_times",
-           "sw_launch_count", "sw_project_static")
+           "sw_launch_count", "sw_project_static", "sw_batch_create", "sw_batch_step",
+           "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -90,6 +91,12 @@ def load(path: str = LIB_PATH):
         "sw_kernel_times": (C.c_int, [H, C.c_int64, _DP, C.POINTER(C.c_int64), _DP]),
         "sw_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "sw_project_static": (C.c_int, [_DP, _DP, C.c_int, C.c_void_p]),
+        "sw_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(H)]),
+        "sw_batch_step": (C.c_int, [H, C.c_int64]),
+        "sw_batch_tune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
+        "sw_batch_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
+        "sw_batch_last_error": (C.c_char_p, [H]),
+        "sw_batch_destroy": (None, [H]),
         "sw_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -259,6 +266,48 @@ def sw_launch_count(h):
     n = C.c_int64()
     _check(load().sw_launch_count(h, C.byref(n)), h)
     return n.value
+
+
+def _bcheck(rc, b):
+    if rc != SW_OK:
+        msg = load().sw_batch_last_error(b)
+        raise SWError(rc, msg.decode() if msg else "")
+
+
+def sw_batch_create(handles):
+    """Batch of handles stepped in shared launches (see include/lagmean.h)."""
+    lib = load()
+    arr = (C.c_void_p * len(handles))(*[h.value for h in handles])
+    b = C.c_void_p()
+    rc = lib.sw_batch_create(arr, len(handles), C.byref(b))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return b
+
+
+def sw_batch_step(b, nsteps):
+    _bcheck(load().sw_batch_step(b, int(nsteps)), b)
+
+
+def sw_batch_tune(b, trial_steps=8):
+    c = C.c_int(-1)
+    _bcheck(load().sw_batch_tune(b, int(trial_steps), C.byref(c)), b)
+    return c.value
+
+
+def sw_batch_launch_count(b):
+    n = C.c_int64()
+    _bcheck(load().sw_batch_launch_count(b, C.byref(n)), b)
+    return n.value
+
+
+def sw_batch_last_error(b):
+    m = load().sw_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def sw_batch_destroy(b):
+    load().sw_batch_destroy(b)
 
 
 def sw_project_static(inp, out, N, stream=None):

@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <vector>
+
 #include "../../include/lagmean.h"
 #include "launch.cuh"
 
@@ -26,11 +28,12 @@ namespace lm {
 void set_handleless_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace lm
 
+struct BatchExec;
+
 struct sw_handle {
   sw_params p;
   Geom g;
   cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   bool fp32 = false;
   size_t tsz = 8;  // sizeof(T)
   std::string err;
@@ -50,14 +53,12 @@ struct sw_handle {
   int64_t done = 0;
   int64_t steps_total = 0;
   Layout L{};
-  // captured graphs of 1 and GRAPH_STEPS RK4 steps for the current layout
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraphExec_t gexec_multi = nullptr;
-  bool graph_valid = false;
-  int64_t kernels_per_step = 0;
+  // launch shapes: column tile 2^lC columns; row_prod Bp rows and ppb
+  // product pairs per block; row_inv Bi rows per block
+  int lC = 2, Bp = 1, ppb = 1, Bi = 1;
+  uint64_t version = 1;  // bumped whenever L or the launch shapes change
+  BatchExec* self = nullptr;  // batch of one used by sw_step / lmean_step
   int64_t launches = 0;  // kernels launched since creation
-  // launch shape of the row pass (rows per block, product pairs per block)
-  int rows_prod = 1, ppb = 1, rows_inv = 1;
 };
 
 static int fail(sw_handle* h, int code, const std::string& msg) {
@@ -173,9 +174,10 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithmic bytes of one launch of each stepping kernel: the distinct input
-// elements it must read and the output elements it must write (box modes
-// NY*KX, mixed rows N*KX, physical N*N), not counting L2 hits or padding.
+// Algorithmic bytes of one launch of each stepping kernel for one run: the
+// distinct input elements it must read and the output elements it must write
+// (box modes NY*KX, mixed rows N*KX, physical N*N), not counting L2 hits or
+// padding.
 struct KBytes {
   double col_inv, row_inv, phys_q, row_prod, col_fwd, update[4];
 };
@@ -228,6 +230,157 @@ struct Prof {
   int n = 0;
 };
 
+// ---------------------------------------------------------------------------
+// Batch executor: the device table of run descriptors, per-kernel block
+// prefix sums and the captured step graphs for a set of handles.
+static const int GRAPH_STEPS = 8;
+static const int SW_K_OF_KT[KT_COUNT] = {SW_K_COL_INV, SW_K_ROW_INV, SW_K_PHYS_Q, SW_K_ROW_PROD, SW_K_COL_FWD,
+                                         SW_K_UPDATE};
+
+struct BatchExec {
+  std::vector<sw_handle*> members;
+  std::vector<uint64_t> versions;
+  bool fp32 = false;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  int nruns = 0;
+  void* d_table = nullptr;  // RunDesc<T>[nruns] then int start[KT_COUNT][nruns+1]
+  size_t table_bytes = 0;
+  int* d_start = nullptr;
+  std::vector<int> start;
+  int threads[KT_COUNT] = {};
+  size_t smem[KT_COUNT] = {};
+  double bytes[KT_COUNT][4] = {};
+  cudaGraphExec_t g1 = nullptr, gm = nullptr;
+  int64_t kernels_per_step = 0;
+  int64_t launches = 0;
+  bool built = false;
+  std::string err;
+};
+
+static void batch_drop_graphs(BatchExec* b) {
+  if (b->g1) cudaGraphExecDestroy(b->g1);
+  if (b->gm) cudaGraphExecDestroy(b->gm);
+  b->g1 = b->gm = nullptr;
+}
+
+static void batch_free(BatchExec* b) {
+  if (!b) return;
+  batch_drop_graphs(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->d_table) cudaFree(b->d_table);
+  delete b;
+}
+
+template <typename T>
+static void fill_desc(sw_handle* h, RunDesc<T>& d) {
+  std::memset(&d, 0, sizeof(d));
+  const Geom& g = h->g;
+  d.g = g;
+  d.L = h->L;
+  d.c = StepConsts{h->p.dt, h->p.f0, h->p.c2, h->p.adv_x, h->p.adv_y};
+  d.y = (cplx<T>*)h->y;
+  d.ysa = (cplx<T>*)h->ys;
+  d.ysb = (cplx<T>*)h->ys2;
+  d.acc = (cplx<T>*)h->acc;
+  d.comp = h->fp32 ? (cplx<T>*)h->comp : nullptr;
+  d.ps = (cplx<T>*)h->ps;
+  d.mix = (cplx<T>*)h->mix;
+  d.pmix = (cplx<T>*)h->pmix;
+  d.phys = (T*)h->phys;
+  d.ef = (const T*)h->ef;
+  d.tw = (const cplx<T>*)h->tw;
+  d.ctr = h->ctr;
+  d.ticket = h->ticket;
+  d.lC = h->lC;
+  d.Bp = h->Bp;
+  d.ppb = h->ppb;
+  d.Bi = h->Bi;
+  const Layout& L = h->L;
+  const int ntile = g.KXP >> h->lC;
+  const int npairs = (L.np + 1) / 2;
+  d.nb[KT_COL_INV] = L.np > 0 ? ntile * L.ni : 0;
+  d.nb[KT_ROW_INV] = (L.np > 0 && L.strategy == 2) ? 2 * (g.N / h->Bi) : 0;
+  d.nb[KT_PHYS_Q] = (L.np > 0 && L.strategy == 2 && L.has_q) ? (int)((g.np + 255) / 256) : 0;
+  d.nb[KT_ROW_PROD] = L.np > 0 ? (g.N / h->Bp) * ((npairs + h->ppb - 1) / h->ppb) : 0;
+  d.nb[KT_COL_FWD] = L.np > 0 ? ntile * L.np : 0;
+  d.nb[KT_UPDATE] = (int)((g.ms + 255) / 256) * L.nf;
+}
+
+// Build (or rebuild) the descriptor table of a batch from its members.
+template <typename T>
+static int batch_build_t(BatchExec* b) {
+  const int n = (int)b->members.size();
+  std::vector<RunDesc<T>> descs(n);
+  for (int k = 0; k < KT_COUNT; ++k) {
+    b->threads[k] = 0;
+    b->smem[k] = 0;
+    for (int st = 0; st < 4; ++st) b->bytes[k][st] = 0.0;
+  }
+  b->start.assign((size_t)KT_COUNT * (n + 1), 0);
+  const size_t cs = sizeof(cplx<T>);
+  for (int r = 0; r < n; ++r) {
+    sw_handle* h = b->members[r];
+    fill_desc<T>(h, descs[r]);
+    const RunDesc<T>& d = descs[r];
+    const int N = h->g.N;
+    const int thr[KT_COUNT] = {((1 << h->lC) * N) / 8, h->Bi * N / 8, 256, h->Bp * N / 8, ((1 << h->lC) * N) / 8, 256};
+    const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * pad8(N) * cs, (size_t)h->Bi * pad8(N) * cs, 0,
+                                 row_prod_smem<T>(N, h->Bp, h->L.strategy), (size_t)(1 << h->lC) * pad8(N) * cs, 0};
+    const KBytes kb = kernel_bytes(h, h->L);
+    const double by[KT_COUNT] = {kb.col_inv, kb.row_inv, kb.phys_q, kb.row_prod, kb.col_fwd, 0.0};
+    for (int k = 0; k < KT_COUNT; ++k) {
+      b->start[(size_t)k * (n + 1) + r + 1] = b->start[(size_t)k * (n + 1) + r] + d.nb[k];
+      if (d.nb[k] == 0) continue;
+      if (b->threads[k] && b->threads[k] != thr[k]) {
+        b->err = "batch members need equal block shapes (grid sizes 64..512, or one grid size)";
+        return SW_EINVAL;
+      }
+      b->threads[k] = thr[k];
+      if (sm[k] > b->smem[k]) b->smem[k] = sm[k];
+      for (int st = 0; st < 4; ++st) b->bytes[k][st] += (k == KT_UPDATE ? kb.update[st] : by[k]);
+    }
+  }
+  const size_t desc_bytes = (sizeof(RunDesc<T>) * n + 255) & ~(size_t)255;
+  const size_t need = desc_bytes + sizeof(int) * b->start.size();
+  if (need > b->table_bytes) {
+    if (b->d_table) cudaFree(b->d_table);
+    b->d_table = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_table, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->table_bytes = 0;
+      b->err = std::string("cudaMalloc (batch table): ") + cudaGetErrorString(e);
+      return SW_ENOMEM;
+    }
+    b->table_bytes = need;
+  }
+  b->d_start = (int*)((char*)b->d_table + desc_bytes);
+  cudaError_t e = cudaMemcpyAsync(b->d_table, descs.data(), sizeof(RunDesc<T>) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_start, b->start.data(), sizeof(int) * b->start.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    b->err = std::string("batch table upload: ") + cudaGetErrorString(e);
+    return SW_ECUDA;
+  }
+  b->nruns = n;
+  b->versions.resize(n);
+  for (int r = 0; r < n; ++r) b->versions[r] = b->members[r]->version;
+  batch_drop_graphs(b);
+  b->built = true;
+  return SW_OK;
+}
+
+static int batch_build(BatchExec* b) { return b->fp32 ? batch_build_t<float>(b) : batch_build_t<double>(b); }
+
+static bool batch_stale(const BatchExec* b) {
+  if (!b->built) return true;
+  for (size_t r = 0; r < b->members.size(); ++r)
+    if (b->versions[r] != b->members[r]->version) return true;
+  return false;
+}
+
 #define LAUNCH(cls_, bytes_, ...)                                    \
   do {                                                               \
     if (pf) cudaEventRecord(pf->ev[2 * pf->n], s);                   \
@@ -241,153 +394,103 @@ struct Prof {
     ++*nlaunch;                                                      \
   } while (0)
 
-// ---------------------------------------------------------------------------
-// Stage pipeline (one RK4 step = 4 stages) for precision T.
+// One RK4 step (4 stages) of every member of the batch.
 template <typename T>
-static cudaError_t enqueue_step(sw_handle* h, cudaStream_t s, Prof* pf, int64_t* nlaunch) {
-  const Layout& L = h->L;
-  const Geom& g = h->g;
-  const KBytes kb = kernel_bytes(h, L);
-  cplx<T>* y = (cplx<T>*)h->y;
-  // stage inputs: stage 1 and 3 read ysa, stage 2 reads ysb
-  cplx<T>* ysa = (cplx<T>*)h->ys;
-  cplx<T>* ysb = (cplx<T>*)h->ys2;
-  StepConsts c{h->p.dt, h->p.f0, h->p.c2, h->p.adv_x, h->p.adv_y};
+static cudaError_t enqueue_batch_step(BatchExec* b, cudaStream_t s, Prof* pf, int64_t* nlaunch) {
+  const RunDesc<T>* runs = (const RunDesc<T>*)b->d_table;
+  const int n = b->nruns;
   cudaError_t e;
+  static const int order[KT_COUNT] = {KT_COL_INV, KT_ROW_INV, KT_PHYS_Q, KT_ROW_PROD, KT_COL_FWD, KT_UPDATE};
   for (int stage = 0; stage < 4; ++stage) {
-    const cplx<T>* src = stage == 0 ? y : (stage == 2 ? ysb : ysa);
-    cplx<T>* dst_next = (stage == 1) ? ysb : ysa;
-    if (L.np > 0) {
-      ColInvArgs<T> ci;
-      ci.src = src;
-      ci.dst = (cplx<T>*)h->mix;
-      ci.tw = (const cplx<T>*)h->tw;
-      ci.g = g;
-      ci.nout = L.ni;
-      for (int i = 0; i < L.ni; ++i) {
-        ci.src_idx[i] = L.i_src[i];
-        ci.src2_idx[i] = L.i_src2[i];
-        ci.op[i] = L.i_op[i];
-        ci.dst_idx[i] = i;
-      }
-      LAUNCH(SW_K_COL_INV, kb.col_inv, launch_col_inv<T>(ci, s));
-      if (L.strategy == 2) {
-        RowInvArgs<T, T> ri;
-        std::memset(&ri, 0, sizeof(ri));
-        ri.src = (const cplx<T>*)h->mix;
-        ri.dst = (T*)h->phys;
-        ri.dst_stride = g.np;
-        ri.tw = (const cplx<T>*)h->tw;
-        ri.g = g;
-        ri.B = h->rows_inv;
-        ri.npairs = 2;
-        ri.a_idx[0] = L.i_u; ri.b_idx[0] = L.i_v; ri.oa[0] = PH_U; ri.ob[0] = PH_V;
-        ri.a_idx[1] = L.i_h; ri.b_idx[1] = L.i_z; ri.oa[1] = PH_H; ri.ob[1] = PH_Z;
-        for (int p = 0; p < 2; ++p) ri.sa[p] = ri.sb[p] = 1.0;
-        LAUNCH(SW_K_ROW_INV, kb.row_inv, launch_row_inv<T, T>(ri, s));
-        if (L.has_q) LAUNCH(SW_K_PHYS_Q, kb.phys_q, launch_phys_q<T>((T*)h->phys, g.np, h->p.f0, s));
-      }
-      RowProdArgs<T> rp;
-      rp.mix = (const cplx<T>*)h->mix;
-      rp.prod = (cplx<T>*)h->pmix;
-      rp.phys = (const T*)h->phys;
-      rp.ctr = h->ctr;
-      rp.tw = (const cplx<T>*)h->tw;
-      rp.g = g;
-      rp.L = L;
-      rp.c = c;
-      rp.B = h->rows_prod;
-      rp.ppb = h->ppb;
-      rp.stage = stage;
-      LAUNCH(SW_K_ROW_PROD, kb.row_prod, launch_row_prod<T>(rp, s));
-      ColFwdArgs<T> cf;
-      cf.src = (const cplx<T>*)h->pmix;
-      cf.dst = (cplx<T>*)h->ps;
-      cf.tw = (const cplx<T>*)h->tw;
-      cf.g = g;
-      cf.nout = L.np;
-      for (int i = 0; i < L.np; ++i) cf.src_idx[i] = cf.dst_idx[i] = i;
-      LAUNCH(SW_K_COL_FWD, kb.col_fwd, launch_col_fwd<T>(cf, s));
+    for (int oi = 0; oi < KT_COUNT; ++oi) {
+      const int k = order[oi];
+      const int total = b->start[(size_t)k * (n + 1) + n];
+      if (total == 0) continue;
+      LAUNCH(SW_K_OF_KT[k], b->bytes[k][stage],
+             launch_stage<T>(k, runs, b->d_start + (size_t)k * (n + 1), n, total, b->threads[k], b->smem[k], stage, s));
     }
-    UpdateArgs<T> ua;
-    ua.y = y;
-    ua.ysin = src;
-    ua.ys = dst_next;
-    ua.acc = (cplx<T>*)h->acc;
-    ua.comp = h->fp32 ? (cplx<T>*)h->comp : nullptr;
-    ua.ps = (const cplx<T>*)h->ps;
-    ua.ef = (const T*)h->ef;
-    ua.ctr = h->ctr;
-    ua.ticket = h->ticket;
-    ua.g = g;
-    ua.L = L;
-    ua.c = c;
-    ua.stage = stage;
-    LAUNCH(SW_K_UPDATE, kb.update[stage], launch_update<T>(ua, s));
   }
   return cudaSuccess;
 }
 
-static const int GRAPH_STEPS = 8;
-
-static void drop_graph(sw_handle* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->gexec_multi) cudaGraphExecDestroy(h->gexec_multi);
-  h->gexec = h->gexec_multi = nullptr;
-  h->graph_valid = false;
-}
-
 // Capture `steps` RK4 steps into an executable graph.  Capture runs on a
 // private stream (the caller's stream may be the legacy default stream, which
-// cannot be captured); the graphs are launched on the caller's stream.
-static int capture_steps(sw_handle* h, int steps, cudaGraphExec_t* out) {
+// cannot be captured); the graphs are launched on the batch's stream.
+static int batch_capture(BatchExec* b, int steps, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
-  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int64_t nl = 0;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < steps && e == cudaSuccess; ++i)
-    e = h->fp32 ? enqueue_step<float>(h, h->cap_stream, nullptr, &nl)
-                : enqueue_step<double>(h, h->cap_stream, nullptr, &nl);
-  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return fail_cuda(h, "enqueue_step (capture)", e);
+  if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    b->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+    return SW_ECUDA;
   }
-  if (e2 != cudaSuccess) return fail_cuda(h, "cudaStreamEndCapture", e2);
+  if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+    b->err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+    return SW_ECUDA;
+  }
+  int64_t nl = 0;
+  for (int i = 0; i < steps && e == cudaSuccess; ++i)
+    e = b->fp32 ? enqueue_batch_step<float>(b, b->cap, nullptr, &nl) : enqueue_batch_step<double>(b, b->cap, nullptr, &nl);
+  cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    b->err = std::string("step capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    return SW_ECUDA;
+  }
   e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     *out = nullptr;
-    return fail_cuda(h, "cudaGraphInstantiate", e);
+    b->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+    return SW_ECUDA;
   }
-  h->kernels_per_step = nl / steps;
+  b->kernels_per_step = nl / steps;
   return SW_OK;
 }
 
-static int ensure_graph(sw_handle* h) {
-  if (h->graph_valid) return SW_OK;
-  drop_graph(h);
-  int rc = capture_steps(h, 1, &h->gexec);
-  if (rc == SW_OK) rc = capture_steps(h, GRAPH_STEPS, &h->gexec_multi);
-  if (rc != SW_OK) {
-    drop_graph(h);
-    return rc;
+static int batch_ready(BatchExec* b) {
+  if (batch_stale(b)) {
+    int rc = batch_build(b);
+    if (rc) return rc;
   }
-  h->graph_valid = true;
+  if (!b->g1) {
+    int rc = batch_capture(b, 1, &b->g1);
+    if (rc == SW_OK) rc = batch_capture(b, GRAPH_STEPS, &b->gm);
+    if (rc != SW_OK) {
+      batch_drop_graphs(b);
+      return rc;
+    }
+  }
+  return SW_OK;
+}
+
+// Replay n steps of the batch (no bookkeeping on the members).
+static int batch_replay(BatchExec* b, int64_t n) {
+  int rc = batch_ready(b);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  int64_t i = 0;
+  for (; e == cudaSuccess && i + GRAPH_STEPS <= n; i += GRAPH_STEPS) e = cudaGraphLaunch(b->gm, b->stream);
+  for (; e == cudaSuccess && i < n; ++i) e = cudaGraphLaunch(b->g1, b->stream);
+  if (e != cudaSuccess) {
+    b->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+    return SW_ECUDA;
+  }
+  b->launches += n * b->kernels_per_step;
   return SW_OK;
 }
 
 static int run_steps(sw_handle* h, int64_t n) {
   if (n <= 0) return SW_OK;
-  int rc = ensure_graph(h);
-  if (rc) return rc;
-  int64_t i = 0;
-  for (; i + GRAPH_STEPS <= n; i += GRAPH_STEPS) CK(h, cudaGraphLaunch(h->gexec_multi, h->stream));
-  for (; i < n; ++i) CK(h, cudaGraphLaunch(h->gexec, h->stream));
+  int rc = batch_replay(h->self, n);
+  if (rc) return fail(h, rc, h->self->err);
   h->steps_total += n;
-  h->launches += n * h->kernels_per_step;
+  h->launches += n * h->self->kernels_per_step;
   return SW_OK;
+}
+
+static void set_layout(sw_handle* h, const Layout& L) {
+  h->L = L;
+  ++h->version;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +534,7 @@ static int spectral_pair_to_phys(sw_handle* h, const OutSpec& a, const OutSpec* 
   ri.dst_stride = g.np;
   ri.tw = h->tw64;
   ri.g = g;
-  ri.B = h->rows_inv;
+  ri.B = h->Bi;
   ri.npairs = 1;
   ri.a_idx[0] = 0;
   ri.b_idx[0] = b ? 1 : -1;
@@ -469,7 +572,7 @@ static int load_ic_from_out64(sw_handle* h) {
   rf.dst = h->mix64;
   rf.tw = h->tw64;
   rf.g = g;
-  rf.B = h->rows_inv;
+  rf.B = h->Bi;
   rf.npairs = 2;
   rf.a_idx[0] = 0; rf.b_idx[0] = 1; rf.oa[0] = 0; rf.ob[0] = 1;
   rf.a_idx[1] = 2; rf.b_idx[1] = -1; rf.oa[1] = 2; rf.ob[1] = -1;
@@ -562,15 +665,20 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   while ((1 << g.log2N) < g.N) ++g.log2N;
   g.K = (g.N - 1) / 3;
   g.KX = g.K + 1;
-  g.KXP = (g.KX + 3) / 4 * 4;
+  // column tiles of C = 2048/N columns (4 at N >= 512, at most 32): C*N is
+  // the same for all grids up to 512, so they can share batched launches
+  h->lC = 2;
+  while ((1 << h->lC) * g.N < 2048 && h->lC < 5) ++h->lC;
+  const int C = 1 << h->lC;
+  g.KXP = (g.KX + C - 1) / C * C;
   g.NY = 2 * g.K + 1;
   g.ms = (long long)g.NY * g.KXP;
   g.mi = (long long)g.N * g.KXP;
   g.np = (long long)g.N * g.N;
   const size_t cs = 2 * h->tsz;  // complex T
   h->diag_blocks = 1024;
-  h->rows_prod = row_block_rows(g.N);
-  h->rows_inv = row_block_rows(g.N);
+  h->Bp = row_block_rows(g.N);
+  h->Bi = row_block_rows(g.N);
   h->ppb = g.N <= 512 ? 1 : MAXP;
   // arena layout
   size_t off = 0;
@@ -625,6 +733,15 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
     return fail(nullptr, SW_ECUDA, m);
   }
   h->L = build_layout(p->model, 0, 0, 0);
+  h->self = new (std::nothrow) BatchExec();
+  if (!h->self) {
+    cudaFree(h->arena);
+    delete h;
+    return fail(nullptr, SW_ENOMEM, "host allocation failed");
+  }
+  h->self->members.push_back(h);
+  h->self->fp32 = h->fp32;
+  h->self->stream = h->stream;
   rc = copy_in_uvh(h, ic_uvh, ic_on_device);
   if (rc == SW_OK) {
     e = cudaStreamSynchronize(h->stream);
@@ -632,6 +749,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   }
   if (rc != SW_OK) {
     std::string m = h->err;
+    batch_free(h->self);
     cudaFree(h->arena);
     delete h;
     return fail(nullptr, rc, m);
@@ -643,8 +761,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
 extern "C" void sw_destroy(sw_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  drop_graph(h);
-  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  batch_free(h->self);
   if (h->arena) cudaFree(h->arena);
   delete h;
 }
@@ -677,8 +794,7 @@ extern "C" int lmean_begin(sw_handle* h, const lm_params* lp) {
   CK(h, cudaMemsetAsync((char*)h->y + 3 * g.ms * cs, 0, (size_t)(MAXF - 3) * g.ms * cs, h->stream));
   CK(h, cudaMemsetAsync(h->comp, 0, (size_t)MAXF * g.ms * cs, h->stream));
   CK(h, cudaMemsetAsync(h->ctr, 0, sizeof(long long), h->stream));
-  drop_graph(h);
-  h->L = L;
+  set_layout(h, L);
   h->lp = *lp;
   h->done = 0;
   h->lm_open = true;
@@ -758,8 +874,7 @@ extern "C" int lmean_end(sw_handle* h, const lm_result* out) {
     if ((rc = copy_out(h, dst[i], i, out->on_device))) return rc;
   if (!out->on_device) CK(h, cudaStreamSynchronize(h->stream));
   h->lm_open = false;
-  drop_graph(h);
-  h->L = build_layout(h->p.model, 0, 0, 0);
+  set_layout(h, build_layout(h->p.model, 0, 0, 0));
   return SW_OK;
 }
 
@@ -822,7 +937,7 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   ri.dst_stride = g.np;
   ri.tw = h->tw64;
   ri.g = g;
-  ri.B = h->rows_inv;
+  ri.B = h->Bi;
   ri.npairs = 1;
   ri.a_idx[0] = 0;
   ri.b_idx[0] = -1;
@@ -915,8 +1030,7 @@ extern "C" int sw_set_state(sw_handle* h, const void* blob, size_t size) {
   long long ctr = hd.done;
   CK(h, cudaMemcpyAsync(h->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  drop_graph(h);
-  h->L = L;
+  set_layout(h, L);
   h->lm_open = hd.lm_open != 0;
   h->lp = hd.lp;
   h->done = hd.done;
@@ -936,6 +1050,11 @@ extern "C" int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUN
     launches[k] = 0;
     bytes[k] = 0.0;
   }
+  BatchExec* b = h->self;
+  if (batch_stale(b)) {
+    int rc = batch_build(b);
+    if (rc) return fail(h, rc, b->err);
+  }
   Prof pf;
   int nev = 0;
   cudaError_t e = cudaSuccess;
@@ -946,7 +1065,7 @@ extern "C" int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUN
   for (int64_t it = 0; rc == SW_OK && it < nsteps; ++it) {
     pf.n = 0;
     int64_t nl = 0;
-    e = h->fp32 ? enqueue_step<float>(h, h->stream, &pf, &nl) : enqueue_step<double>(h, h->stream, &pf, &nl);
+    e = h->fp32 ? enqueue_batch_step<float>(b, h->stream, &pf, &nl) : enqueue_batch_step<double>(b, h->stream, &pf, &nl);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
       rc = fail_cuda(h, "sw_kernel_times step", e);
@@ -968,6 +1087,182 @@ extern "C" int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUN
   }
   for (int i = 0; i < nev; ++i) cudaEventDestroy(pf.ev[i]);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batches
+struct sw_batch {
+  BatchExec* ex = nullptr;
+  std::string err;
+  int tuned = -1;
+};
+
+static int bfail(sw_batch* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+extern "C" int sw_batch_create(sw_handle* const* handles, int n, sw_batch** out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, SW_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!handles || n < 1) return fail(nullptr, SW_EINVAL, "a batch needs at least one handle");
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return fail(nullptr, SW_EINVAL, "NULL handle in batch");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(nullptr, SW_EINVAL, "handle repeated in batch");
+    if (handles[i]->fp32 != handles[0]->fp32) return fail(nullptr, SW_EINVAL, "batch members differ in precision");
+    if (handles[i]->stream != handles[0]->stream) return fail(nullptr, SW_EINVAL, "batch members differ in stream");
+  }
+  sw_batch* b = new (std::nothrow) sw_batch();
+  BatchExec* ex = b ? new (std::nothrow) BatchExec() : nullptr;
+  if (!ex) {
+    delete b;
+    return fail(nullptr, SW_ENOMEM, "host allocation failed");
+  }
+  b->ex = ex;
+  ex->members.assign(handles, handles + n);
+  ex->fp32 = handles[0]->fp32;
+  ex->stream = handles[0]->stream;
+  int rc = batch_build(ex);
+  if (rc != SW_OK) {
+    std::string m = ex->err;
+    batch_free(ex);
+    delete b;
+    return fail(nullptr, rc, m);
+  }
+  *out = b;
+  return SW_OK;
+}
+
+extern "C" int sw_batch_step(sw_batch* b, int64_t nsteps) {
+  if (!b) return SW_EINVAL;
+  b->err.clear();
+  if (nsteps < 0) return bfail(b, SW_EINVAL, "nsteps < 0");
+  for (sw_handle* h : b->ex->members)
+    if (h->lm_open && nsteps > h->lp.n_steps - h->done)
+      return bfail(b, SW_ERANGE, "more steps than remain in a member's interval");
+  if (nsteps == 0) return SW_OK;
+  int rc = batch_replay(b->ex, nsteps);
+  if (rc) return bfail(b, rc, b->ex->err);
+  for (sw_handle* h : b->ex->members) {
+    h->steps_total += nsteps;
+    if (h->lm_open) h->done += nsteps;
+  }
+  return SW_OK;
+}
+
+// Save / restore the evolving state of the members around tuning trials.
+struct Saved {
+  void* buf = nullptr;
+  size_t fb = 0;
+  long long ctr = 0;
+};
+
+extern "C" int sw_batch_tune(sw_batch* b, int trial_steps, int* choice) {
+  if (!b) return SW_EINVAL;
+  b->err.clear();
+  if (trial_steps < 1) return bfail(b, SW_EINVAL, "trial_steps must be >= 1");
+  BatchExec* ex = b->ex;
+  int maxN = 0;
+  for (sw_handle* h : ex->members) maxN = h->g.N > maxN ? h->g.N : maxN;
+  const int pts[3] = {512, 1024, 2048};
+  const int ppbs[4] = {1, 2, 3, MAXP};
+  std::vector<Saved> saved(ex->members.size());
+  cudaError_t e = cudaSuccess;
+  int rc = SW_OK;
+  for (size_t i = 0; i < ex->members.size() && rc == SW_OK; ++i) {
+    sw_handle* h = ex->members[i];
+    saved[i].fb = (size_t)MAXF * h->g.ms * 2 * h->tsz;
+    if ((e = cudaMalloc(&saved[i].buf, 2 * saved[i].fb)) != cudaSuccess) {
+      cudaGetLastError();
+      saved[i].buf = nullptr;
+      rc = bfail(b, SW_ENOMEM, std::string("cudaMalloc (tuning copy): ") + cudaGetErrorString(e));
+      break;
+    }
+    if ((e = cudaMemcpyAsync(saved[i].buf, h->y, saved[i].fb, cudaMemcpyDeviceToDevice, ex->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((char*)saved[i].buf + saved[i].fb, h->comp, saved[i].fb, cudaMemcpyDeviceToDevice,
+                             ex->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&saved[i].ctr, h->ctr, sizeof(long long), cudaMemcpyDeviceToHost, ex->stream)) != cudaSuccess)
+      rc = bfail(b, SW_ECUDA, std::string("tuning save: ") + cudaGetErrorString(e));
+  }
+  if (rc == SW_OK && (e = cudaStreamSynchronize(ex->stream)) != cudaSuccess)
+    rc = bfail(b, SW_ECUDA, std::string("tuning save: ") + cudaGetErrorString(e));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == SW_OK && ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess))
+    rc = bfail(b, SW_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+  int best = -1;
+  float best_ms = 0.f;
+  for (int ci = 0; rc == SW_OK && ci < 12; ++ci) {
+    const int P = pts[ci / 4], ppb = ppbs[ci % 4];
+    if (P < maxN && ci / 4 > 0) continue;  // same shape as a smaller P for the largest member
+    for (sw_handle* h : ex->members) {
+      h->Bp = row_block_rows(h->g.N, P);
+      h->ppb = ppb;
+      ++h->version;
+    }
+    rc = batch_ready(ex);
+    if (rc) {
+      rc = bfail(b, rc, ex->err);
+      break;
+    }
+    if ((e = cudaEventRecord(e0, ex->stream)) != cudaSuccess) break;
+    rc = batch_replay(ex, trial_steps);
+    if (rc) {
+      rc = bfail(b, rc, ex->err);
+      break;
+    }
+    if ((e = cudaEventRecord(e1, ex->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+    if (best < 0 || t < best_ms) {
+      best = ci;
+      best_ms = t;
+    }
+  }
+  if (rc == SW_OK && e != cudaSuccess) rc = bfail(b, SW_ECUDA, std::string("tuning trial: ") + cudaGetErrorString(e));
+  if (best < 0) best = 0;
+  for (sw_handle* h : ex->members) {
+    h->Bp = row_block_rows(h->g.N, pts[best / 4]);
+    h->ppb = ppbs[best % 4];
+    ++h->version;
+  }
+  // restore the saved states
+  for (size_t i = 0; i < ex->members.size(); ++i) {
+    sw_handle* h = ex->members[i];
+    if (!saved[i].buf) continue;
+    if (rc == SW_OK) {
+      if ((e = cudaMemcpyAsync(h->y, saved[i].buf, saved[i].fb, cudaMemcpyDeviceToDevice, ex->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(h->comp, (char*)saved[i].buf + saved[i].fb, saved[i].fb, cudaMemcpyDeviceToDevice,
+                               ex->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(h->ctr, &saved[i].ctr, sizeof(long long), cudaMemcpyHostToDevice, ex->stream)) != cudaSuccess)
+        rc = bfail(b, SW_ECUDA, std::string("tuning restore: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t es = cudaStreamSynchronize(ex->stream);
+  if (rc == SW_OK && es != cudaSuccess) rc = bfail(b, SW_ECUDA, std::string("tuning restore: ") + cudaGetErrorString(es));
+  for (auto& sv : saved)
+    if (sv.buf) cudaFree(sv.buf);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->tuned = best;
+  if (choice) *choice = best;
+  return rc;
+}
+
+extern "C" int sw_batch_launch_count(sw_batch* b, int64_t* count) {
+  if (!b || !count) return SW_EINVAL;
+  *count = b->ex->launches;
+  return SW_OK;
+}
+
+extern "C" const char* sw_batch_last_error(sw_batch* b) { return b ? b->err.c_str() : ""; }
+
+extern "C" void sw_batch_destroy(sw_batch* b) {
+  if (!b) return;
+  if (b->ex) cudaStreamSynchronize(b->ex->stream);
+  batch_free(b->ex);
+  delete b;
 }
 
 extern "C" int sw_launch_count(sw_handle* h, int64_t* count) {

@@ -1,7 +1,7 @@
-// launch.cuh -- host-side launchers for the kernels of kernels.cuh.
-// Instantiated once per precision (kernels_f32.cu, kernels_f64.cu).
+// launch.cuh -- host-side launchers for the kernels of kernels.cuh and
+// stage.cuh.  Instantiated once per precision (kernels_f32.cu, kernels_f64.cu).
 #pragma once
-#include "kernels.cuh"
+#include "stage.cuh"
 
 namespace lm {
 
@@ -23,9 +23,9 @@ template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStr
 template <typename T> cudaError_t launch_col_fwd(const ColFwdArgs<T>& a, cudaStream_t s);
 template <typename T, typename TO> cudaError_t launch_row_inv(const RowInvArgs<T, TO>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_row_prod(const RowProdArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_update(const UpdateArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_phys_q(T* phys, long long np, double f0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
+                         size_t smem, int stage, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s);
@@ -46,7 +46,10 @@ template <typename T> static cudaError_t prepare_kernels_t() {
   if ((e = cudaFuncSetAttribute(k_col_fwd<T>, A, mx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_row_inv<T, T>, A, mx)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_row_fwd<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_row_prod<T>, A, mx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_col_inv<T>, A, mx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_col_fwd<T>, A, mx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_row_inv<T>, A, mx)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_stage_row_prod<T>, A, mx)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -76,30 +79,24 @@ template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStr
   return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_row_prod(const RowProdArgs<T>& a, cudaStream_t s) {
-  const size_t sm = row_prod_smem<T>(a.g.N, a.B, a.L.strategy);
-  const int npairs = (a.L.np + 1) / 2;
-  dim3 grid(a.g.N / a.B, (npairs + a.ppb - 1) / a.ppb);
-  k_row_prod<T><<<grid, a.B * a.g.N / 8, sm, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T> cudaError_t launch_update(const UpdateArgs<T>& a, cudaStream_t s) {
-  const int thr = 256;
-  const long long nb = (a.g.ms + thr - 1) / thr;
-  k_update<T><<<dim3((unsigned)nb, a.L.nf), thr, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T> cudaError_t launch_phys_q(T* phys, long long np, double f0, cudaStream_t s) {
-  k_phys_q<T><<<(unsigned)((np + 255) / 256), 256, 0, s>>>(phys, np, f0);
+template <typename T>
+cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
+                         size_t smem, int stage, cudaStream_t s) {
+  switch (kt) {
+    case KT_COL_INV: k_stage_col_inv<T><<<blocks, threads, smem, s>>>(runs, start, nruns, stage); break;
+    case KT_ROW_INV: k_stage_row_inv<T><<<blocks, threads, smem, s>>>(runs, start, nruns); break;
+    case KT_PHYS_Q: k_stage_phys_q<T><<<blocks, threads, 0, s>>>(runs, start, nruns); break;
+    case KT_ROW_PROD: k_stage_row_prod<T><<<blocks, threads, smem, s>>>(runs, start, nruns, stage); break;
+    case KT_COL_FWD: k_stage_col_fwd<T><<<blocks, threads, smem, s>>>(runs, start, nruns); break;
+    default: k_stage_update<T><<<blocks, threads, 0, s>>>(runs, start, nruns, stage); break;
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s) {
-  k_spec_to_f64<T><<<(unsigned)((ms + 255) / 256), 256, 0, s>>>(y, comp, out, ms, 0, nullptr, fa, fb, scale);
+  k_spec_to_f64<T><<<(unsigned)((ms + 255) / 256), 256, 0, s>>>(y, comp, out, ms, fa, fb, scale);
   return cudaGetLastError();
 }
 
@@ -108,16 +105,15 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
   return cudaGetLastError();
 }
 
-#define LM_INSTANTIATE_ALL(T)                                                                             \
-  template cudaError_t launch_col_inv<T>(const ColInvArgs<T>&, cudaStream_t);                             \
-  template cudaError_t launch_col_fwd<T>(const ColFwdArgs<T>&, cudaStream_t);                             \
-  template cudaError_t launch_row_inv<T, T>(const RowInvArgs<T, T>&, cudaStream_t);                       \
-  template cudaError_t launch_row_fwd<T>(const RowFwdArgs<T>&, cudaStream_t);                             \
-  template cudaError_t launch_row_prod<T>(const RowProdArgs<T>&, cudaStream_t);                           \
-  template cudaError_t launch_update<T>(const UpdateArgs<T>&, cudaStream_t);                              \
-  template cudaError_t launch_phys_q<T>(T*, long long, double, cudaStream_t);                             \
-  template cudaError_t launch_spec_to_f64<T>(const cplx<T>*, const cplx<T>*, double2*, long long, int, int, \
-                                             double, cudaStream_t);                                       \
+#define LM_INSTANTIATE_ALL(T)                                                                               \
+  template cudaError_t launch_col_inv<T>(const ColInvArgs<T>&, cudaStream_t);                               \
+  template cudaError_t launch_col_fwd<T>(const ColFwdArgs<T>&, cudaStream_t);                               \
+  template cudaError_t launch_row_inv<T, T>(const RowInvArgs<T, T>&, cudaStream_t);                         \
+  template cudaError_t launch_row_fwd<T>(const RowFwdArgs<T>&, cudaStream_t);                               \
+  template cudaError_t launch_stage<T>(int, const RunDesc<T>*, const int*, int, int, int, size_t, int,     \
+                                       cudaStream_t);                                                       \
+  template cudaError_t launch_spec_to_f64<T>(const cplx<T>*, const cplx<T>*, double2*, long long, int, int,  \
+                                             double, cudaStream_t);                                         \
   template cudaError_t launch_spec_from_f64<T>(const double2*, cplx<T>*, long long, cudaStream_t);
 #endif
 
