@@ -242,6 +242,81 @@ const char* sw_batch_last_error(sw_batch* b);
 /* Release the batch (not its members; synchronises).  NULL: no-op. */
 void sw_batch_destroy(sw_batch* b);
 
+/* ---- serving: a continuous-batching request loop on one GPU -------------------
+ * A server owns a host thread that admits Lagrangian-mean jobs (one averaging
+ * interval each, any grid size, window, strategy and field set) in arrival
+ * order while the job-state memory stays within hbm_budget bytes and the
+ * active jobs within max_active; it keeps each admitted job's state resident
+ * on the device, steps all active jobs together in batched launches
+ * (sw_batch, grouped by compatible block shapes) in rounds of at most
+ * chunk_steps steps, and completes each job as its interval ends (lmean_end
+ * into the job's host buffers, then the job's device memory is released).
+ * Jobs that arrive while others run join the next round.  A job's result is
+ * the same as that of the same job run alone. */
+typedef struct sw_server sw_server;
+
+typedef struct sw_server_params {
+  int32_t precision;   /* SW_PREC_FP32 or SW_PREC_FP64 for every job        */
+  int32_t max_active;  /* concurrent jobs on the device, >= 1               */
+  int32_t chunk_steps; /* RK4 steps per round, >= 1                          */
+  int32_t reserved;    /* must be 0                                         */
+  int64_t hbm_budget;  /* bytes of device memory for job state, > 0         */
+  void* stream;        /* cudaStream_t for all job work (NULL: a private one) */
+} sw_server_params;
+
+typedef struct sw_job {
+  sw_params params;      /* the job's grid and model (precision must match)   */
+  lm_params lm;          /* its averaging interval                             */
+  const double* ic_uvh;  /* host, 3*N*N doubles; read at admission            */
+  lm_result out;         /* host output buffers (on_device = 0); written at
+                            completion; must stay valid until then            */
+  int64_t tag;           /* caller's identifier, returned with the job        */
+} sw_job;
+
+typedef struct sw_job_done {
+  int64_t tag;
+  int32_t status;        /* SW_OK, or the error that ended the job            */
+  int32_t reserved;
+  double t_submit;       /* seconds on the server clock (sw_server_clock)     */
+  double t_admit;
+  double t_done;
+  int64_t bytes;         /* device bytes the job held                          */
+} sw_job_done;
+
+typedef struct sw_server_stats {
+  int64_t submitted, completed, failed, active, queued;
+  int64_t grid_point_steps; /* sum of N^2 * steps over completed jobs          */
+  int64_t bytes_in_use, peak_bytes;
+  int64_t rounds;           /* batched step rounds                             */
+} sw_server_stats;
+
+/* Start a server (its thread uses the calling thread's current device).
+ * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA (message via sw_last_error(NULL)). */
+int sw_server_create(const sw_server_params* p, sw_server** out);
+
+/* Queue a job (thread-safe; the descriptor is copied).  SW_EINVAL for an
+ * invalid job or one whose state alone exceeds the budget, SW_ESTATE after
+ * shutdown began. */
+int sw_server_submit(sw_server* s, const sw_job* job);
+
+/* Collect up to max finished jobs into done[0..*n); waits up to wait_ms
+ * milliseconds for at least one if none is ready (0: do not wait). */
+int sw_server_poll(sw_server* s, sw_job_done* done, int max, int* n, int wait_ms);
+
+/* Counters (thread-safe). */
+int sw_server_stats_get(sw_server* s, sw_server_stats* st);
+
+/* Seconds since the server was created (monotonic). */
+double sw_server_clock(sw_server* s);
+
+/* Stop the loop: jobs still queued are dropped (their results are not
+ * written), active jobs are released; then free the server.  NULL: no-op. */
+void sw_server_destroy(sw_server* s);
+
+/* Device bytes a handle with these parameters holds (the unit of the
+ * server's HBM budget); 0 for invalid parameters. */
+int64_t sw_state_bytes(const sw_params* p);
+
 /* ---- allocation-free projection --------------------------------------------
  * The paper has no counterpart to this call; it is a library convenience.
  * Some callers cannot allocate device memory: code running where a

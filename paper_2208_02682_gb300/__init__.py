@@ -11,5 +11,6 @@ from .api import (  # noqa: F401
     lmean_step, lmean_end, lmean_progress, sw_get_fields, sw_set_fields, sw_diag,
     sw_get_state, sw_set_state, sw_time, sw_sync, sw_last_error, sw_version, sw_kernel_times,
     sw_launch_count, sw_project_static, sw_batch_create, sw_batch_step, sw_batch_tune,
-    sw_batch_launch_count, sw_batch_last_error, sw_batch_destroy,
+    sw_batch_launch_count, sw_batch_last_error, sw_batch_destroy, sw_server_create, sw_server_submit,
+    sw_server_poll, sw_server_stats_get, sw_server_clock, sw_server_destroy, sw_state_bytes,
 )

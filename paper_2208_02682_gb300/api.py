@@ -27,7 +27,9 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
            "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version", "sw_kernel_times",
            "sw_launch_count", "sw_project_static", "sw_batch_create", "sw_batch_step",
-           "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy")
+           "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
+           "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
+           "sw_server_clock", "sw_server_destroy", "sw_state_bytes")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -52,6 +54,27 @@ class lm_result(C.Structure):
                 ("pos_x", _DP), ("pos_y", _DP),
                 ("e_zeta", _DP), ("e_h", _DP), ("e_u", _DP), ("e_v", _DP), ("e_q", _DP),
                 ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class sw_server_params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_active", C.c_int32), ("chunk_steps", C.c_int32),
+                ("reserved", C.c_int32), ("hbm_budget", C.c_int64), ("stream", C.c_void_p)]
+
+
+class sw_job(C.Structure):
+    _fields_ = [("params", sw_params), ("lm", lm_params), ("ic_uvh", _DP), ("out", lm_result),
+                ("tag", C.c_int64)]
+
+
+class sw_job_done(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("bytes", C.c_int64)]
+
+
+class sw_server_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "active", "queued",
+                                         "grid_point_steps", "bytes_in_use", "peak_bytes", "rounds")]
 
 
 class SWError(RuntimeError):
@@ -97,6 +120,13 @@ def load(path: str = LIB_PATH):
         "sw_batch_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "sw_batch_last_error": (C.c_char_p, [H]),
         "sw_batch_destroy": (None, [H]),
+        "sw_server_create": (C.c_int, [C.POINTER(sw_server_params), C.POINTER(H)]),
+        "sw_server_submit": (C.c_int, [H, C.POINTER(sw_job)]),
+        "sw_server_poll": (C.c_int, [H, C.POINTER(sw_job_done), C.c_int, C.POINTER(C.c_int), C.c_int]),
+        "sw_server_stats_get": (C.c_int, [H, C.POINTER(sw_server_stats)]),
+        "sw_server_clock": (C.c_double, [H]),
+        "sw_server_destroy": (None, [H]),
+        "sw_state_bytes": (C.c_int64, [C.POINTER(sw_params)]),
         "sw_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -308,6 +338,88 @@ def sw_batch_last_error(b):
 
 def sw_batch_destroy(b):
     load().sw_batch_destroy(b)
+
+
+def sw_state_bytes(params: sw_params) -> int:
+    return int(load().sw_state_bytes(C.byref(params)))
+
+
+class Server:
+    """Handle of a running sw_server plus the host buffers of its jobs (kept
+    alive here until each job completes)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.pending = {}
+
+
+def sw_server_create(precision="f32", max_active=16, chunk_steps=32, hbm_budget=150 << 30, stream=None):
+    lib = load()
+    p = sw_server_params()
+    p.precision = {"f64": SW_PREC_FP64, "f32": SW_PREC_FP32}[precision]
+    p.max_active, p.chunk_steps, p.reserved = int(max_active), int(chunk_steps), 0
+    p.hbm_budget = int(hbm_budget)
+    p.stream = stream or 0
+    sp = C.c_void_p()
+    rc = lib.sw_server_create(C.byref(p), C.byref(sp))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return Server(sp)
+
+
+def sw_server_submit(s: Server, params: sw_params, lp: lm_params, ic_uvh, out: dict, tag: int):
+    """Queue a job; ic_uvh (3, N, N) and the host output arrays in `out` are
+    kept referenced until the job is polled as done."""
+    ic = np.ascontiguousarray(ic_uvh, dtype=np.float64)
+    j = sw_job()
+    j.params = params
+    j.lm = lp
+    j.ic_uvh = ic.ctypes.data_as(_DP)
+    r = lm_result()
+    for k in RESULT_KEYS:
+        a = out.get(k)
+        if a is not None:
+            p, d = _ptr(a)
+            if d:
+                raise ValueError("server outputs are host arrays")
+            setattr(r, k, p)
+    r.on_device = 0
+    j.out = r
+    j.tag = int(tag)
+    rc = load().sw_server_submit(s.ptr, C.byref(j))
+    if rc != SW_OK:
+        raise SWError(rc, "job rejected")
+    s.pending[int(tag)] = (ic, out)
+
+
+def sw_server_poll(s: Server, max_jobs=256, wait_ms=0):
+    buf = (sw_job_done * max_jobs)()
+    n = C.c_int(0)
+    rc = load().sw_server_poll(s.ptr, buf, max_jobs, C.byref(n), int(wait_ms))
+    if rc != SW_OK:
+        raise SWError(rc, "poll failed")
+    res = []
+    for i in range(n.value):
+        d = buf[i]
+        ic, out = s.pending.pop(int(d.tag), (None, None))
+        res.append(dict(tag=d.tag, status=d.status, t_submit=d.t_submit, t_admit=d.t_admit,
+                        t_done=d.t_done, bytes=d.bytes, out=out))
+    return res
+
+
+def sw_server_stats_get(s: Server) -> dict:
+    st = sw_server_stats()
+    load().sw_server_stats_get(s.ptr, C.byref(st))
+    return {n: getattr(st, n) for n, _ in sw_server_stats._fields_}
+
+
+def sw_server_clock(s: Server) -> float:
+    return load().sw_server_clock(s.ptr)
+
+
+def sw_server_destroy(s: Server):
+    load().sw_server_destroy(s.ptr)
+    s.pending.clear()
 
 
 def sw_project_static(inp, out, N, stream=None):

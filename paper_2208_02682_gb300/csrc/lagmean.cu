@@ -616,6 +616,63 @@ static int validate(const sw_params* p, std::string& why) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static const int DIAG_BLOCKS = 1024;
+
+// Grid geometry: cutoff K, column tiles of C = 2048/N columns (4 at
+// N >= 512, at most 32: C*N is the same for all grids up to 512, so they can
+// share batched launches) and the padded column count KXP (a multiple of C).
+static void plan_geometry(int N, Geom& g, int& lC) {
+  g.N = N;
+  g.log2N = 0;
+  while ((1 << g.log2N) < g.N) ++g.log2N;
+  g.K = (g.N - 1) / 3;
+  g.KX = g.K + 1;
+  lC = 2;
+  while ((1 << lC) * g.N < 2048 && lC < 5) ++lC;
+  const int C = 1 << lC;
+  g.KXP = (g.KX + C - 1) / C * C;
+  g.NY = 2 * g.K + 1;
+  g.ms = (long long)g.NY * g.KXP;
+  g.mi = (long long)g.N * g.KXP;
+  g.np = (long long)g.N * g.N;
+}
+
+// Offsets of the handle's device arena (256-byte aligned slices).
+struct ArenaPlan {
+  size_t o[19];
+  size_t total;
+};
+
+static ArenaPlan plan_arena(const Geom& g, size_t tsz) {
+  ArenaPlan A;
+  const size_t cs = 2 * tsz;
+  const size_t sizes[19] = {
+      MAXF * g.ms * cs, MAXF * g.ms * cs, MAXF * g.ms * cs, MAXF * g.ms * cs,  // y, ys, ys2, acc
+      MAXF * g.ms * cs, MAXP * g.ms * cs,                                      // comp, ps
+      MAXI * g.mi * cs, MAXP * g.mi * cs,                                      // mix, pmix
+      NPH * g.np * tsz, 2 * g.ms * tsz, g.N * cs,                              // phys, ef, tw
+      g.N * sizeof(double2), 4 * g.ms * sizeof(double2),                       // tw64, spec64
+      4 * g.mi * sizeof(double2), 12 * g.np * sizeof(double),                  // mix64, out64
+      2 * DIAG_BLOCKS * sizeof(double), 4 * sizeof(double),                    // part, dres
+      sizeof(long long), sizeof(unsigned)};                                    // ctr, ticket
+  size_t off = 0;
+  for (int i = 0; i < 19; ++i) {
+    A.o[i] = off;
+    off += align256(sizes[i]);
+  }
+  A.total = off;
+  return A;
+}
+
+extern "C" int64_t sw_state_bytes(const sw_params* p) {
+  std::string why;
+  if (validate(p, why) != SW_OK) return 0;
+  Geom g;
+  int lC;
+  plan_geometry(p->N, g, lC);
+  return (int64_t)plan_arena(g, p->precision == SW_PREC_FP32 ? 4 : 8).total;
+}
+
 template <typename T>
 static void host_tables(const sw_params& p, const Geom& g, void* ef_host, void* tw_host, double2* tw64_host) {
   T* ef = (T*)ef_host;
@@ -660,38 +717,18 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   h->fp32 = p->precision == SW_PREC_FP32;
   h->tsz = h->fp32 ? 4 : 8;
   Geom& g = h->g;
-  g.N = p->N;
-  g.log2N = 0;
-  while ((1 << g.log2N) < g.N) ++g.log2N;
-  g.K = (g.N - 1) / 3;
-  g.KX = g.K + 1;
-  // column tiles of C = 2048/N columns (4 at N >= 512, at most 32): C*N is
-  // the same for all grids up to 512, so they can share batched launches
-  h->lC = 2;
-  while ((1 << h->lC) * g.N < 2048 && h->lC < 5) ++h->lC;
-  const int C = 1 << h->lC;
-  g.KXP = (g.KX + C - 1) / C * C;
-  g.NY = 2 * g.K + 1;
-  g.ms = (long long)g.NY * g.KXP;
-  g.mi = (long long)g.N * g.KXP;
-  g.np = (long long)g.N * g.N;
+  plan_geometry(p->N, g, h->lC);
   const size_t cs = 2 * h->tsz;  // complex T
-  h->diag_blocks = 1024;
+  h->diag_blocks = DIAG_BLOCKS;
   h->Bp = row_block_rows(g.N);
   h->Bi = row_block_rows(g.N);
   h->ppb = g.N <= 512 ? 1 : MAXP;
-  // arena layout
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-  const size_t o_y = take(MAXF * g.ms * cs), o_ys = take(MAXF * g.ms * cs), o_ys2 = take(MAXF * g.ms * cs);
-  const size_t o_acc = take(MAXF * g.ms * cs);
-  const size_t o_comp = take(MAXF * g.ms * cs), o_ps = take(MAXP * g.ms * cs);
-  const size_t o_mix = take(MAXI * g.mi * cs), o_pmix = take(MAXP * g.mi * cs);
-  const size_t o_phys = take(NPH * g.np * h->tsz), o_ef = take(2 * g.ms * h->tsz), o_tw = take(g.N * cs);
-  const size_t o_tw64 = take(g.N * sizeof(double2)), o_spec64 = take(4 * g.ms * sizeof(double2));
-  const size_t o_mix64 = take(4 * g.mi * sizeof(double2)), o_out64 = take(12 * g.np * sizeof(double));
-  const size_t o_part = take(2 * h->diag_blocks * sizeof(double)), o_dres = take(4 * sizeof(double));
-  const size_t o_ctr = take(sizeof(long long)), o_ticket = take(sizeof(unsigned));
+  const ArenaPlan A = plan_arena(g, h->tsz);
+  const size_t o_y = A.o[0], o_ys = A.o[1], o_ys2 = A.o[2], o_acc = A.o[3], o_comp = A.o[4], o_ps = A.o[5];
+  const size_t o_mix = A.o[6], o_pmix = A.o[7], o_phys = A.o[8], o_ef = A.o[9], o_tw = A.o[10];
+  const size_t o_tw64 = A.o[11], o_spec64 = A.o[12], o_mix64 = A.o[13], o_out64 = A.o[14];
+  const size_t o_part = A.o[15], o_dres = A.o[16], o_ctr = A.o[17], o_ticket = A.o[18];
+  const size_t off = A.total;
   h->arena_bytes = off;
   cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
   if (e != cudaSuccess) {

@@ -43,15 +43,18 @@ def test_library_exports_every_declared_symbol(lm):
 def test_struct_layout_matches_c(tmp_path, lm):
     prog = tmp_path / "sz.c"
     prog.write_text('#include "lagmean.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(sw_params),"
+                    "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(sw_params),"
                     " sizeof(lm_params), sizeof(lm_result), offsetof(sw_params, dt),"
-                    " offsetof(lm_result, on_device)); return 0;}\n")
+                    " offsetof(lm_result, on_device), sizeof(sw_server_params), sizeof(sw_job),"
+                    " offsetof(sw_job, tag), sizeof(sw_job_done), sizeof(sw_server_stats)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     api = lm.api
     assert got == [C.sizeof(api.sw_params), C.sizeof(api.lm_params), C.sizeof(api.lm_result),
-                   api.sw_params.dt.offset, api.lm_result.on_device.offset]
+                   api.sw_params.dt.offset, api.lm_result.on_device.offset,
+                   C.sizeof(api.sw_server_params), C.sizeof(api.sw_job), api.sw_job.tag.offset,
+                   C.sizeof(api.sw_job_done), C.sizeof(api.sw_server_stats)]
 
 
 @pytest.mark.parametrize("field,value", [("N", 48), ("N", 8), ("N", 4096), ("dt", 0.0), ("dt", -1.0),
@@ -65,6 +68,17 @@ def test_invalid_parameters_rejected_before_device_use(lm, field, value):
         lm.sw_create(p, ic)
     assert ei.value.code == lm.api.SW_EINVAL
     assert lm.sw_last_error(None)
+
+
+def test_state_bytes_and_server_validation(lm):
+    # the budget unit grows with the grid and halves in FP32; invalid -> 0
+    b = [lm.sw_state_bytes(lm.make_params(N, 1e-3, precision="f32")) for N in (64, 128, 256)]
+    assert 0 < b[0] < b[1] < b[2]
+    assert lm.sw_state_bytes(lm.make_params(64, 1e-3, precision="f64")) > b[0]
+    p = lm.make_params(48, 1e-3)
+    assert lm.sw_state_bytes(p) == 0
+    with pytest.raises(lm.SWError):
+        lm.sw_server_create(max_active=0)
 
 
 def test_null_handle_is_rejected(lm):
