@@ -154,6 +154,140 @@ def config_dict(w, form):
 
 
 # ------------------------------------------------------------------------------
+def measure_batched(lm, torch, sample_steps=48, warm=8):
+    """Ensemble of 64 runs, N uniform in {128, 256, 512}, Ro uniform in
+    [0.05, 0.2], FP32, Strategy 1, stepped as one autotuned batch; beside it
+    the plain single-run FP64 form (one 256^2 run, same fields)."""
+    rng = np.random.Generator(np.random.PCG64(1004))
+    sizes = rng.choice([128, 256, 512], size=64)
+    ros = rng.uniform(0.05, 0.2, size=64)
+    n_interval = si.interval_steps(3.6, 4.0, 5e-3)
+    hs = []
+    for i, (N, ro) in enumerate(zip(sizes, ros)):
+        K = (int(N) - 1) // 3
+        ic = np.ascontiguousarray(np.stack(si.turbulence_plus_waves(int(N), float(ro), 1.0, 4.0, 6.0, 2000 + i)))
+        h = lm.sw_create(lm.make_params(int(N), 5e-3, precision="f32", nu8=10.0 / K ** 8), ic)
+        lm.lmean_begin(h, lm.make_lm_params(1, FIELDS, pos=True, eulerian=True, n_steps=n_interval))
+        hs.append(h)
+    b = lm.sw_batch_create(hs)
+    choice = lm.sw_batch_tune(b, 4)
+    lm.sw_batch_step(b, warm)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lm.sw_batch_step(b, sample_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pts = int(sum(int(N) * int(N) for N in sizes))
+    batched = pts * sample_steps / (ms * 1e-3)
+    lm.sw_batch_destroy(b)
+    for h in hs:
+        lm.sw_destroy(h)
+    # plain single-run FP64 form
+    w = workload()
+    ic = np.ascontiguousarray(np.stack(w.initial_condition()))
+    h = lm.sw_create(lm.make_params(w.N, w.dt, precision="f64", nu8=w.nu8), ic)
+    lm.lmean_begin(h, lm.make_lm_params(1, FIELDS, pos=True, eulerian=True, n_steps=n_interval))
+    lm.lmean_step(h, warm)
+    torch.cuda.synchronize()
+    e0.record()
+    lm.lmean_step(h, sample_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    lm.sw_destroy(h)
+    plain64 = w.N * w.N * sample_steps / (ms64 * 1e-3)
+    return {"value": batched, "unit": UNIT, "runs": 64, "grid_points": pts,
+            "sizes": {str(n): int((sizes == n).sum()) for n in (128, 256, 512)},
+            "sample_steps": sample_steps, "tuned_shape": choice,
+            "plain_fp64_single_256": plain64, "ratio_vs_plain_fp64": batched / plain64,
+            "workload": "64-run ensemble, N uniform in {128,256,512}, Ro uniform in [0.05,0.2], FP32, "
+                        "Strategy 1 (zeta,h,u,v, positions, Eulerian), one batch per RK stage kernel"}
+
+
+def measure_precision(lm, torch):
+    """1024^2 precision form: one 3.6-period interval (waves |k| 8-12, Ro 0.05,
+    ratio 2) in FP32 and FP64 on the GPU; per-field relative L2 of FP32."""
+    w = si.WORKLOADS["precision-1024"]
+    N, n = w.N, w.n_steps
+    ic = np.ascontiguousarray(np.stack(w.initial_condition()))
+    res, times = {}, {}
+    for prec in ("f32", "f64"):
+        h = lm.sw_create(lm.make_params(N, w.dt, precision=prec, nu8=w.nu8), ic)
+        lm.lmean_begin(h, lm.make_lm_params(1, FIELDS, pos=True, eulerian=True, n_steps=n))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lm.lmean_step(h, n)
+        e1.record()
+        torch.cuda.synchronize()
+        times[prec] = e0.elapsed_time(e1)
+        out = {k: np.zeros((N, N)) for k in OUT_KEYS}
+        lm.lmean_end(h, out)
+        lm.sw_destroy(h)
+        res[prec] = out
+    x = 2 * np.pi * np.arange(N) / N
+    X = x[None, :] + 0 * x[:, None]
+    Y = x[:, None] + 0 * x[None, :]
+    err = {}
+    for k in OUT_KEYS:
+        a, b = res["f32"][k], res["f64"][k]
+        if k in ("h", "e_h"):
+            a, b = a - 1.0, b - 1.0
+        elif k == "pos_x":
+            a, b = a - X, b - X
+        elif k == "pos_y":
+            a, b = a - Y, b - Y
+        err[k] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"N": N, "n_steps": n, "rel_l2_fp32_vs_fp64": err, "max_rel_l2": max(err.values()),
+            "gp_steps_per_s": {p: N * N * n / (t * 1e-3) for p, t in times.items()},
+            "workload": "1024^2, Ro 0.05, waves |k| 8-12, ratio 2, Strategy 1, one interval"}
+
+
+def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
+    """Poisson stream of Lagrangian-mean requests through sw_server."""
+    import time as _t
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for i in range(n_jobs):
+        N = int(rng.choice(sizes))
+        periods = float(rng.uniform(1.0, 8.0))
+        strat = int(rng.choice([1, 2]))
+        dt = 5e-3 if N <= 1024 else 2.5e-3
+        n = si.interval_steps(periods, 4.0, dt)
+        K = (N - 1) // 3
+        ic = np.stack(si.turbulence_plus_waves(N, 0.1, 1.0, 4.0, 6.0, 3000 + i))
+        out = {k: np.zeros((N, N)) for k in ("zeta", "h", "u", "v", "pos_x", "pos_y")}
+        jobs.append((N, dt, K, n, strat, ic, out))
+    gaps = rng.exponential(1.0 / rate, size=n_jobs)
+    srv = lm.sw_server_create("f32", max_active=64, chunk_steps=32, hbm_budget=150 << 30)
+    t_start = _t.time()
+    t_next = t_start
+    for i, (N, dt, K, n, strat, ic, out) in enumerate(jobs):
+        t_next += gaps[i]
+        d = t_next - _t.time()
+        if d > 0:
+            _t.sleep(d)
+        lm.sw_server_submit(srv, lm.make_params(N, dt, precision="f32", nu8=10.0 / K ** 8),
+                            lm.make_lm_params(strat, ("zeta", "h", "u", "v"), n_steps=n), ic, out, tag=i)
+    done = []
+    while len(done) < n_jobs and _t.time() - t_start < 600:
+        done += lm.sw_server_poll(srv, wait_ms=100)
+    st = lm.sw_server_stats_get(srv)
+    lm.sw_server_destroy(srv)
+    lat = np.array([d["t_done"] - d["t_submit"] for d in done])
+    t0 = min(d["t_submit"] for d in done)
+    t1 = max(d["t_done"] for d in done)
+    offered = sum(j[0] * j[0] * j[3] for j in jobs) / (n_jobs / rate)
+    return {"jobs": n_jobs, "completed": st["completed"], "failed": st["failed"],
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "throughput": st["grid_point_steps"] / (t1 - t0), "unit": UNIT,
+            "offered_load": offered, "peak_bytes": st["peak_bytes"], "rounds": st["rounds"],
+            "workload": f"Poisson {rate:g} req/s, N uniform in {list(sizes)}, windows U[1,8] wave periods, "
+                        "strategy 1 or 2, FP32, 150 GB budget, %d requests" % n_jobs}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -298,6 +432,12 @@ def run_ours(args):
     for h in hs:
         lm.sw_destroy(h)
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = measure_batched(lm, torch)
+        extras["precision_form"] = measure_precision(lm, torch)
+        extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -316,6 +456,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "kernels": kernel_share, "wall_s": t_wall,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -330,6 +471,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, precision and served figures")
+    ap.add_argument("--serve-jobs", type=int, default=24)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
