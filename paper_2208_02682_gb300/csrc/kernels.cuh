@@ -189,7 +189,8 @@ __device__ void row_pair_forward_store(cplx<T>* buf, cplx<T>* __restrict__ da,
 
 // ---------------------------------------------------------------------------
 // Row pass, inverse: physical outputs from pairs of mixed fields, with an
-// affine epilogue out = scale*val + ax*x + ay*y (used for the mean positions).
+// affine epilogue out = scale*val + ax*x + ay*y + c (mean positions; the
+// depth h = 1 + eta from the stored perturbation eta).
 template <typename T, typename TO>
 struct RowInvArgs {
   const cplx<T>* src;  // mixed, stride mi
@@ -203,6 +204,7 @@ struct RowInvArgs {
   int oa[8], ob[8];        // output field indices (-1: skip)
   double sa[8], sb[8];     // scales
   double axa[8], aya[8], axb[8], ayb[8];
+  double ca[8], cb[8];  // constant offsets
 };
 
 template <typename T, typename TO>
@@ -225,10 +227,10 @@ __global__ void __launch_bounds__(256) k_row_inv(const __grid_constant__ RowInvA
       const long long off = (long long)y * N + x;
       if (a.oa[p] >= 0)
         a.dst[a.oa[p] * a.dst_stride + off] =
-            (TO)(a.sa[p] * (double)v.x + a.axa[p] * (x * dxg) + a.aya[p] * (y * dxg));
+            (TO)(a.sa[p] * (double)v.x + a.axa[p] * (x * dxg) + a.aya[p] * (y * dxg) + a.ca[p]);
       if (a.ob[p] >= 0)
         a.dst[a.ob[p] * a.dst_stride + off] =
-            (TO)(a.sb[p] * (double)v.y + a.axb[p] * (x * dxg) + a.ayb[p] * (y * dxg));
+            (TO)(a.sb[p] * (double)v.y + a.axb[p] * (x * dxg) + a.ayb[p] * (y * dxg) + a.cb[p]);
     }
     __syncthreads();
   }
@@ -318,6 +320,9 @@ __global__ void k_spec_to_f64(const cplx<T>* __restrict__ y, const cplx<T>* __re
     out[q * ms + m] = make_double2(re * scale, im * scale);
   }
 }
+
+// Add delta to the real part of one spectral coefficient (mean depth).
+__global__ void k_add_real(double2* p, double delta);
 
 // FP64 spectral -> T spectral (initial condition).
 template <typename T>

@@ -60,6 +60,15 @@ __global__ void __launch_bounds__(256) k_diag_final(const double* __restrict__ p
   }
 }
 
+__global__ void k_add_real(double2* p, double delta) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) p->x += delta;
+}
+
+cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s) {
+  k_add_real<<<1, 1, 0, s>>>(p, delta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag(const double* phys, long long np, double f0, double c2, double* part, int nblk,
                         double* out, cudaStream_t s) {
   k_diag_partial<<<nblk, 256, 0, s>>>(phys, np, f0, c2, part);

@@ -502,6 +502,7 @@ struct OutSpec {
   int field;  // evolved-field index (-1: none)
   double scale, ax, ay;
   int slot;   // output slot in out64
+  double cst; // constant added (1 for the depth h = 1 + eta)
 };
 
 static int spectral_pair_to_phys(sw_handle* h, const OutSpec& a, const OutSpec* b) {
@@ -543,10 +544,12 @@ static int spectral_pair_to_phys(sw_handle* h, const OutSpec& a, const OutSpec* 
   ri.sa[0] = a.scale;
   ri.axa[0] = a.ax;
   ri.aya[0] = a.ay;
+  ri.ca[0] = a.cst;
   if (b) {
     ri.sb[0] = b->scale;
     ri.axb[0] = b->ax;
     ri.ayb[0] = b->ay;
+    ri.cb[0] = b->cst;
   }
   CK(h, launch_row_inv<double, double>(ri, s));
   h->launches += 3;
@@ -585,9 +588,12 @@ static int load_ic_from_out64(sw_handle* h) {
   cf.nout = 3;
   for (int i = 0; i < 3; ++i) cf.src_idx[i] = cf.dst_idx[i] = i;
   CK(h, launch_col_fwd<double>(cf, s));
+  // the state holds the depth perturbation eta = h - 1 (mean depth 1 removed
+  // from the k = 0 mode), which keeps its relative precision in FP32
+  CK(h, launch_add_real(h->spec64 + 2 * g.ms + (long long)g.K * g.KXP, -1.0, s));
   if (h->fp32) CK(h, launch_spec_from_f64<float>(h->spec64, (cplx<float>*)h->y, 3 * g.ms, s));
   else CK(h, launch_spec_from_f64<double>(h->spec64, (cplx<double>*)h->y, 3 * g.ms, s));
-  h->launches += 3;
+  h->launches += 4;
   return SW_OK;
 }
 
@@ -886,7 +892,7 @@ extern "C" int lmean_end(sw_handle* h, const lm_result* out) {
   int n = 0;
   for (int j = 0; j < L.nlm; ++j)
     if (lm_ptr[L.lmf[j]]) {
-      os[n] = OutSpec{L.f_g[j], 1.0 / T, 0.0, 0.0, n};
+      os[n] = OutSpec{L.f_g[j], 1.0 / T, 0.0, 0.0, n, L.lmf[j] == LMF_H ? 1.0 : 0.0};
       dst[n++] = lm_ptr[L.lmf[j]];
     }
   if (L.has_pos) {
@@ -895,14 +901,14 @@ extern "C" int lmean_end(sw_handle* h, const lm_result* out) {
       if (pp[c]) {
         // S1: Xi^{-1} = x - D/T;  S2: Xi = x + xi
         const double sc = L.strategy == 1 ? -1.0 / T : 1.0;
-        os[n] = OutSpec{L.f_p[c], sc, c == 0 ? 1.0 : 0.0, c == 1 ? 1.0 : 0.0, n};
+        os[n] = OutSpec{L.f_p[c], sc, c == 0 ? 1.0 : 0.0, c == 1 ? 1.0 : 0.0, n, 0.0};
         dst[n++] = pp[c];
       }
   }
   if (L.eulerian)
     for (int j = 0; j < L.nlm; ++j)
       if (e_ptr[L.lmf[j]]) {
-        os[n] = OutSpec{L.f_e[j], 1.0 / T, 0.0, 0.0, n};
+        os[n] = OutSpec{L.f_e[j], 1.0 / T, 0.0, 0.0, n, L.lmf[j] == LMF_H ? 1.0 : 0.0};
         dst[n++] = e_ptr[L.lmf[j]];
       }
   int rc = phys_outputs(h, os, n);
@@ -919,7 +925,7 @@ extern "C" int sw_get_fields(sw_handle* h, double* uvh, int on_device) {
   if (!h) return SW_EINVAL;
   h->err.clear();
   if (!uvh) return fail(h, SW_EINVAL, "uvh is NULL");
-  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0}, {h->L.f_v, 1.0, 0, 0, 1}, {h->L.f_h, 1.0, 0, 0, 2}};
+  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, 1.0}};
   // the dynamics fields carry no compensation term (it stays zero)
   int rc = phys_outputs(h, os, 3);
   if (rc) return rc;
@@ -945,7 +951,7 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   h->err.clear();
   if (!out) return fail(h, SW_EINVAL, "out is NULL");
   // physical u, v, h, zeta in FP64: zeta via a spectral curl in FP64
-  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0}, {h->L.f_v, 1.0, 0, 0, 1}, {h->L.f_h, 1.0, 0, 0, 2}};
+  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, 1.0}};
   int rc = phys_outputs(h, os, 3);
   if (rc) return rc;
   // zeta = i kx v - i ky u from FP64 copies of u, v
@@ -992,7 +998,8 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   CK(h, cudaMemcpyAsync(m0, (char*)h->y + ((size_t)h->L.f_h * g.ms + (size_t)g.K * g.KXP) * cs, cs,
                         cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  out[0] = h->fp32 ? (double)((float*)m0)[0] : ((double*)m0)[0];
+  // the state holds eta = h - 1
+  out[0] = 1.0 + (h->fp32 ? (double)((float*)m0)[0] : ((double*)m0)[0]);
   out[1] = res[1];
   out[2] = res[2];
   return SW_OK;

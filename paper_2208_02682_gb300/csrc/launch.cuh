@@ -32,6 +32,7 @@ cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* o
 template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T>* y, long long n, cudaStream_t s);
 cudaError_t launch_diag(const double* phys, long long np, double f0, double c2, double* part, int nblk,
                         double* out, cudaStream_t s);
+cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s);
 
 #ifdef LM_INSTANTIATE
 // Raise the dynamic shared-memory limit of every kernel once (outside any

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
   }
 }
 
-// q = (f0 + zeta)/h into the gather buffer (Strategy 2 with PV averaged).
+// q = (f0 + zeta)/h, h = 1 + eta, into the gather buffer (Strategy 2 with PV
+// averaged).
 template <typename T>
 __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restrict__ runs,
                                                       const int* __restrict__ start, int nruns) {
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
   const RunDesc<T>& d = runs[r];
   const long long i = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
   const long long np = d.g.np;
-  if (i < np) d.phys[PH_Q * np + i] = ((T)d.c.f0 + d.phys[PH_Z * np + i]) / d.phys[PH_H * np + i];
+  if (i < np) d.phys[PH_Q * np + i] = ((T)d.c.f0 + d.phys[PH_Z * np + i]) / ((T)1 + d.phys[PH_H * np + i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,9 +225,10 @@ __global__ void __launch_bounds__(256) k_stage_row_prod(const RunDesc<T>* __rest
         case PK_ZV: val = z * v; break;
         case PK_ZU: val = z * u; break;
         case PK_KE: val = (T)0.5 * (u * u + v * v); break;
-        case PK_HU: val = h * u; break;
-        case PK_HV: val = h * v; break;
-        case PK_Q: val = (f0 + z) / h; break;
+        // depth h = 1 + eta; the state and the row buffers hold eta
+        case PK_HU: val = u + h * u; break;
+        case PK_HV: val = v + h * v; break;
+        case PK_Q: val = (f0 + z) / ((T)1 + h); break;
         case PK_ADV: {
           // u.grad G (Eq. gtilde-evol) or u.grad D
           const cplx<T> dd = W[rr * bst + pad8(x)];
