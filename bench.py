@@ -88,6 +88,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def slowest_rank(value, dist=None, device=None):
+    """Maximum of a per-rank time over all ranks (replicas: the job ends with
+    the slowest one).  Without a process group, the value itself."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def workload():
     w = si.WORKLOADS["plain-256"]
     return w
@@ -355,13 +372,9 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
     launches = sum(lm.sw_launch_count(h) for h in hs) - launches0
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
     gp_per_step = len(hs) * N * N * n
-    value = world * gp_per_step * args.steps / (ms * 1e-3)
+    value = replica_throughput(gp_per_step * args.steps, world, ms * 1e-3)
 
     # per-kernel device times (kernels launched one by one, same stream)
     ktimes = {}
@@ -419,12 +432,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             e2e_interval()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * gp_per_step * args.steps / te, "unit": UNIT,
+        te = slowest_rank(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": replica_throughput(gp_per_step * args.steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": len(hs) * ic.nbytes,
                "d2h_bytes_per_step": len(hs) * len(OUT_KEYS) * N * N * 8,
                "note": "sw_set_fields from pinned host memory + interval + lmean_end to pinned host"}
