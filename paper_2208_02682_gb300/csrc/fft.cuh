@@ -52,16 +52,34 @@ __device__ __forceinline__ void dft8(cplx<T>* v) {
   v[3] = cadd<T>(a3, b3); v[7] = csub<T>(a3, b3);
 }
 
-// Twiddles w^{r k}, r < R, of one butterfly from at most three table loads
-// (w^k, w^2k, w^4k); the others are products of those (at most two
+// Twiddle exp(sigma 2 pi i e 2^tstep / N).  From the table (host FP64
+// values rounded to T), or, with TWC and FP32, from sincospif: that removes
+// the scattered table loads of the late passes, whose L1 wavefronts limit
+// kernels with many resident warps (the column passes); kernels with few
+// resident warps (the row passes) hide table loads better than the longer
+// sincospif chain.  The argument e 2^(tstep+1-log2N) is exact in FP32.
+template <typename T, int SIGN, bool TWC>
+__device__ __forceinline__ cplx<T> twiddle(int e, int tstep, int log2N, const cplx<T>* __restrict__ tw) {
+  cplx<T> t;
+  if (TWC && sizeof(T) == 4) {
+    float s, c;
+    sincospif(ldexpf((float)e, tstep + 1 - log2N), &s, &c);
+    t.x = (T)c;
+    t.y = (T)(-s);
+  } else {
+    t = __ldg(&tw[e << tstep]);
+  }
+  if (SIGN > 0) t.y = -t.y;
+  return t;
+}
+
+// Twiddles w^{r k}, r < R, of one butterfly from three evaluations (w^k,
+// w^2k, w^4k); the others are products of those (at most two
 // multiplications deep).
-template <typename T, int SIGN, int R>
-__device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int tstep, const cplx<T>* __restrict__ tw) {
-  auto ld = [&](int e) {
-    cplx<T> t = __ldg(&tw[e << tstep]);
-    if (SIGN > 0) t.y = -t.y;
-    return t;
-  };
+template <typename T, int SIGN, int R, bool TWC>
+__device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int tstep, int log2N,
+                                                   const cplx<T>* __restrict__ tw) {
+  auto ld = [&](int e) { return twiddle<T, SIGN, TWC>(e, tstep, log2N, tw); };
   w[1] = ld(k);
   if (R >= 4) {
     w[2] = ld(2 * k);
@@ -75,7 +93,7 @@ __device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int tstep,
   }
 }
 
-template <typename T, int SIGN, int LR>
+template <typename T, int SIGN, int LR, bool TWC>
 __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, int bstride,
                                               const cplx<T>* __restrict__ tw) {
   constexpr int R = 1 << LR;
@@ -100,7 +118,7 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
     for (int r = 0; r < R; ++r) v[u * R + r] = src[pad8(j + r * NR)];
     if (k > 0) {
       cplx<T> w[R];
-      butterfly_twiddles<T, SIGN, R>(w, k, tstep, tw);
+      butterfly_twiddles<T, SIGN, R, TWC>(w, k, tstep, log2N, tw);
 #pragma unroll
       for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], w[r]);
     }
@@ -126,18 +144,19 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
 
 // Block-wide FFT of `batch` transforms of length 2^log2N; requires
 // blockDim.x * 8 == batch * 2^log2N and log2N >= 1.  Callers synchronise
-// before (data in place); the function ends with a barrier.
-template <typename T, int SIGN>
+// before (data in place); the function ends with a barrier.  TWC: computed
+// FP32 twiddles (see twiddle()).
+template <typename T, int SIGN, bool TWC = false>
 __device__ void block_fft(cplx<T>* buf, int log2N, int bstride, const cplx<T>* __restrict__ tw) {
   int lNs = 0;
   int rem = log2N;
   while (rem >= 3) {
-    stockham_pass<T, SIGN, 3>(buf, log2N, lNs, bstride, tw);
+    stockham_pass<T, SIGN, 3, TWC>(buf, log2N, lNs, bstride, tw);
     lNs += 3;
     rem -= 3;
   }
-  if (rem == 2) stockham_pass<T, SIGN, 2>(buf, log2N, lNs, bstride, tw);
-  if (rem == 1) stockham_pass<T, SIGN, 1>(buf, log2N, lNs, bstride, tw);
+  if (rem == 2) stockham_pass<T, SIGN, 2, TWC>(buf, log2N, lNs, bstride, tw);
+  if (rem == 1) stockham_pass<T, SIGN, 1, TWC>(buf, log2N, lNs, bstride, tw);
 }
 
 }  // namespace lm

@@ -30,15 +30,14 @@ __device__ void col_inverse_tile(cplx<T>* buf, const cplx<T>* __restrict__ s1, c
   const int N = g.N, K = g.K, KXP = g.KXP;
   const int C = 1 << lC, bst = pad8(N);
   const int nthr = blockDim.x, tid = threadIdx.x;
-  for (int i = tid; i < C * bst; i += nthr) buf[i] = mk<T>(0, 0);
-  __syncthreads();
-  for (int e = tid; e < g.NY * C; e += nthr) {
-    const int kyi = e >> lC, c = e & (C - 1);
+  // every element written once: op(S) at n = ky mod N for |ky| <= K, else 0
+  for (int e = tid; e < N * C; e += nthr) {
+    const int n = e >> lC, c = e & (C - 1);
     const int kx = kx0 + c;
-    const int ky = kyi - K;
-    const long long m = (long long)kyi * KXP + kx;
+    const int ky = n <= K ? n : n - N;
     cplx<T> v = mk<T>(0, 0);
-    if (kx <= K) {
+    if (kx <= K && (n <= K || n >= N - K)) {
+      const long long m = (long long)(ky + K) * KXP + kx;
       cplx<T> x = s1[m];
       if (op == OP_ID) v = x;
       else if (op == OP_DX) v = cik<T>(x, (T)kx);
@@ -48,10 +47,10 @@ __device__ void col_inverse_tile(cplx<T>* buf, const cplx<T>* __restrict__ s1, c
         v = csub<T>(cik<T>(y, (T)kx), cik<T>(x, (T)ky));
       }
     }
-    buf[c * bst + pad8(ky & (N - 1))] = v;
+    buf[c * bst + pad8(n)] = v;
   }
   __syncthreads();
-  block_fft<T, +1>(buf, g.log2N, bst, tw);
+  block_fft<T, +1, true>(buf, g.log2N, bst, tw);
   for (int e = tid; e < N * C; e += nthr) {
     const int n = e >> lC, c = e & (C - 1);
     d[(long long)n * KXP + kx0 + c] = buf[c * bst + pad8(n)];
@@ -70,7 +69,7 @@ __device__ void col_forward_tile(cplx<T>* buf, const cplx<T>* __restrict__ s, cp
     buf[c * bst + pad8(n)] = s[(long long)n * KXP + kx0 + c];
   }
   __syncthreads();
-  block_fft<T, -1>(buf, g.log2N, bst, tw);
+  block_fft<T, -1, true>(buf, g.log2N, bst, tw);
   const T inv = (T)1 / (T)N;
   for (int e = tid; e < g.NY * C; e += nthr) {
     const int kyi = e >> lC, c = e & (C - 1);
@@ -137,18 +136,23 @@ __device__ void row_pair_inverse(cplx<T>* buf, const cplx<T>* __restrict__ ma,
   const int N = g.N, K = g.K, KXP = g.KXP;
   const int bst = pad8(N);
   const int nthr = blockDim.x, tid = threadIdx.x;
-  for (int i = tid; i < B * bst; i += nthr) buf[i] = mk<T>(0, 0);
-  __syncthreads();
+  // Z(k) = A + iB and Z(N-k) = conj(A) + i conj(B) for k <= K (each input
+  // read once); the band K < n < N-K is zeroed.  The two writes never touch
+  // the same element, so no barrier separates them.
+  const int nz = N - 2 * K - 1;
+  for (int e = tid; e < B * nz; e += nthr) {
+    const int r = e / nz, n = K + 1 + (e - r * nz);
+    buf[r * bst + pad8(n)] = mk<T>(0, 0);
+  }
   for (int e = tid; e < B * (K + 1); e += nthr) {
     const int r = e / (K + 1), k = e - r * (K + 1);
     const long long off = (long long)(row0 + r) * KXP + k;
-    cplx<T> A = ma[off];
-    cplx<T> Bv = mb ? mb[off] : mk<T>(0, 0);
+    const cplx<T> A = ma[off];
+    const cplx<T> Bv = mb ? mb[off] : mk<T>(0, 0);
     cplx<T>* z = buf + r * bst;
     if (k == 0) {
       z[0] = mk<T>(A.x, Bv.x);
     } else {
-      // Z(k) = A + iB, Z(N-k) = conj(A) + i conj(B)
       z[pad8(k)] = mk<T>(A.x - Bv.y, A.y + Bv.x);
       z[pad8(N - k)] = mk<T>(A.x + Bv.y, -A.y + Bv.x);
     }
