@@ -72,12 +72,13 @@ class ParticleTracker:
             elif f == "v":
                 vals[f] = v
             elif f == "h":
+                # the oracle state carries eta = h - 1, and so do its means
                 vals[f] = fourier_eval(hh, K, px, py)
             elif f == "zeta":
                 vals[f] = fourier_eval(zh, K, px, py)
             elif f == "q":
                 zeta = fourier_eval(zh, K, px, py)
-                h = fourier_eval(hh, K, px, py)
+                h = 1.0 + fourier_eval(hh, K, px, py)
                 vals[f] = (o.f0 + zeta) / h
         return u, v, vals
 

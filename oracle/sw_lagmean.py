@@ -14,7 +14,10 @@ arXiv 2208.02682) it follows.
 What is computed (one averaging interval [tau, tau+T], Sec. 2, Eq. (ave)):
 
 * the shallow-water dynamics, Sec. 4.2, Eq. (sw_eqs_dimless), written with
-  f0 = 1/Ro and c2 = g H = 1/Fr^2, in vector-invariant form
+  f0 = 1/Ro and c2 = g H = 1/Fr^2, for the depth perturbation eta = h - 1
+  (the mean depth is the scale H, so h = 1 + eta; carrying eta instead of h
+  keeps its digits: averages of h are eta averages plus 1), in
+  vector-invariant form
   u_t = (f0 + zeta) v - d_x(c2 h + |u|^2/2), v_t = -(f0 + zeta) u - d_y(...),
   h_t = -div(h u), zeta = d_x v - d_y u (Sec. 4.2.1 prints d_x u for the second
   term; read as d_y u); the Laplacian viscosity is replaced by a hyperviscosity
@@ -84,7 +87,9 @@ class SWOracle:
         self.t = 0.0
         self.uh = self.spec(np.asarray(u, dtype=np.float64))
         self.vh = self.spec(np.asarray(v, dtype=np.float64))
+        # depth perturbation eta = h - 1 (spectral)
         self.hh = self.spec(np.asarray(h, dtype=np.float64))
+        self.hh[0, 0] -= 1.0
         self.lm = None
 
     # -- transforms --------------------------------------------------------
@@ -150,19 +155,20 @@ class SWOracle:
         """Right-hand sides of all evolved fields at interval time s = t - tau."""
         if self._stage_hook is not None:
             self._stage_hook(st)
-        uh, vh, hh = st["sw"]
+        uh, vh, hh = st["sw"]  # hh: depth perturbation eta
         zh = self.dx(vh) - self.dy(uh)
         u = self.phys(uh)
         v = self.phys(vh)
-        h = self.phys(hh)
+        eta = self.phys(hh)
         zeta = self.phys(zh)
         out = {}
         if self.model == "sw":
-            # Eq. (sw_momentum_dimless), (sw_mass_dimless), vector-invariant form.
+            # Eq. (sw_momentum_dimless), (sw_mass_dimless), vector-invariant form;
+            # grad h = grad eta and h u = u + eta u.
             B = self.c2 * hh + self.spec(0.5 * (u * u + v * v))
             Nu = self.f0 * vh + self.spec(zeta * v) - self.dx(B)
             Nv = -self.f0 * uh - self.spec(zeta * u) - self.dy(B)
-            Nh = -self.dx(self.spec(h * u)) - self.dy(self.spec(h * v))
+            Nh = -self.dx(self.spec(u + eta * u)) - self.dy(self.spec(v + eta * v))
             au, av = u, v
             uh_adv, vh_adv = uh, vh
         else:
@@ -178,10 +184,12 @@ class SWOracle:
         if lm is None:
             return out
         need_q = "q" in lm["fields"]
-        fphys = {"zeta": zeta, "h": h, "u": u, "v": v}
+        # the average of h is carried as the average of eta (the constant
+        # 1 contributes exactly s = t - tau to g and E; added at the end)
+        fphys = {"zeta": zeta, "h": eta, "u": u, "v": v}
         fhat = {"zeta": zh, "h": hh, "u": uh, "v": vh}
         if need_q:
-            fphys["q"] = (self.f0 + zeta) / h  # potential vorticity, Sec. 4.2.1
+            fphys["q"] = (self.f0 + zeta) / (1.0 + eta)  # potential vorticity, Sec. 4.2.1
             fhat["q"] = self.spec(fphys["q"])
         if lm["strategy"] == 1:
             # Eq. (gtilde-evol): d_t g = f - u.grad g.
@@ -307,8 +315,9 @@ class SWOracle:
             raise RuntimeError("interval not complete")
         T = lm["n_steps"] * self.dt
         out = {}
+        one = {"h": 1.0}
         for f in lm["fields"]:
-            out[f] = self.phys(lm["G"][f]) / T
+            out[f] = self.phys(lm["G"][f]) / T + one.get(f, 0.0)
         X = self.x[None, :] + 0.0 * self.x[:, None]
         Y = self.x[:, None] + 0.0 * self.x[None, :]
         if lm["pos"]:
@@ -322,13 +331,13 @@ class SWOracle:
                 out["pos_y"] = Y + self.phys(lm["P"][1])
         if lm["eulerian"]:
             for f in lm["fields"]:
-                out["E_" + f] = self.phys(lm["E"][f]) / T
+                out["E_" + f] = self.phys(lm["E"][f]) / T + one.get(f, 0.0)
         self.lm = None
         return out
 
     # -- diagnostics -------------------------------------------------------
     def fields(self):
-        return self.phys(self.uh), self.phys(self.vh), self.phys(self.hh)
+        return self.phys(self.uh), self.phys(self.vh), 1.0 + self.phys(self.hh)
 
     def diag(self):
         """Domain means: mass <h>, energy <h|u|^2/2 + c2 h^2/2>, potential
@@ -341,7 +350,7 @@ class SWOracle:
                 float(np.mean(0.5 * h * q * q)))
 
     def spectral_state(self):
-        """Copy of the spectral SW state (kx >= 0 half-plane arrays)."""
+        """Copy of the spectral SW state (u, v, eta; kx >= 0 half-plane arrays)."""
         return self.uh.copy(), self.vh.copy(), self.hh.copy()
 
 

@@ -37,20 +37,27 @@ cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s);
 #ifdef LM_INSTANTIATE
 // Raise the dynamic shared-memory limit of every kernel once (outside any
 // stream capture), to the device's opt-in maximum.
+template <typename K> static cudaError_t allow_dynamic_smem(K kern, int optin) {
+  // static and dynamic shared memory together may not exceed the opt-in limit
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 template <typename T> static cudaError_t prepare_kernels_t() {
   int dev = 0, mx = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if ((e = cudaFuncSetAttribute(k_col_inv<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_col_fwd<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_row_inv<T, T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_row_fwd<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_col_inv<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_col_fwd<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_row_inv<T>, A, mx)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_stage_row_prod<T>, A, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_col_inv<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_col_fwd<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_row_inv<T, T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_row_fwd<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_col_inv<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_col_fwd<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_inv<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_prod<T>, mx)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

@@ -50,6 +50,25 @@ __device__ __forceinline__ int find_run(const int* __restrict__ start, int nruns
   return lo;
 }
 
+// Copy the block's run descriptor into shared memory with one cooperative
+// load, so the kernel's many field-index and pointer lookups are shared-memory
+// reads instead of chains of dependent global loads.
+template <typename T>
+__device__ __forceinline__ const RunDesc<T>& load_desc(const RunDesc<T>* __restrict__ runs, int r,
+                                                       unsigned char* sbuf) {
+  static_assert(sizeof(RunDesc<T>) % sizeof(int) == 0, "descriptor size");
+  const int* src = reinterpret_cast<const int*>(runs + r);
+  int* dst = reinterpret_cast<int*>(sbuf);
+  constexpr int n = (int)(sizeof(RunDesc<T>) / sizeof(int));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+  return *reinterpret_cast<const RunDesc<T>*>(sbuf);
+}
+
+#define LM_STAGE_DESC(T_)                                                 \
+  __shared__ __align__(16) unsigned char sdesc_[sizeof(RunDesc<T_>)];   \
+  const RunDesc<T_>& d = load_desc<T_>(runs, r, sdesc_)
+
 template <typename T>
 __device__ __forceinline__ const cplx<T>* stage_input(const RunDesc<T>& d, int stage) {
   return stage == 0 ? d.y : (stage == 2 ? d.ysb : d.ysa);
@@ -300,7 +319,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restrict__ runs,
                                                       const int* __restrict__ start, int nruns, int stage) {
   const int r = find_run(start, nruns, blockIdx.x);
-  const RunDesc<T>& d = runs[r];
+  LM_STAGE_DESC(T);  // many field lookups per thread: read from shared memory
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int lb = blockIdx.x - start[r];
