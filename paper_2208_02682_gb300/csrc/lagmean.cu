@@ -624,19 +624,22 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static const int DIAG_BLOCKS = 1024;
 
-// Grid geometry: cutoff K, column tiles of C = 2048/N columns (4 at
-// N >= 512, at most 32: C*N is the same for all grids up to 512, so they can
-// share batched launches) and the padded column count KXP (a multiple of C).
+// Grid geometry: cutoff K, column tiles of C = 2048/N columns (at most 32:
+// C*N is the same for all grids up to 2048, so they can share batched
+// launches) and the padded column count KXP (a multiple of C and of 4).
 static void plan_geometry(int N, Geom& g, int& lC) {
   g.N = N;
   g.log2N = 0;
   while ((1 << g.log2N) < g.N) ++g.log2N;
   g.K = (g.N - 1) / 3;
   g.KX = g.K + 1;
-  lC = 2;
+  // C = 2048/N columns (at most 32): every column block holds 2048
+  // elements (256 threads); KXP stays a multiple of 4 for the generic passes
+  lC = 0;
   while ((1 << lC) * g.N < 2048 && lC < 5) ++lC;
   const int C = 1 << lC;
-  g.KXP = (g.KX + C - 1) / C * C;
+  const int pad = C > 4 ? C : 4;
+  g.KXP = (g.KX + pad - 1) / pad * pad;
   g.NY = 2 * g.K + 1;
   g.ms = (long long)g.NY * g.KXP;
   g.mi = (long long)g.N * g.KXP;
