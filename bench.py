@@ -3,8 +3,8 @@
 
 One bench step is one averaging interval (lmean_begin, n_steps RK4 steps,
 lmean_end) of the 256^2 turbulence-plus-Poincare-wave workload, Strategies 1
-and 2 side by side on two CUDA streams, FP32 stepping with FP64 end-of-interval
-recovery.  Metric: grid-point-steps/s = runs * N^2 * RK4 steps / device time.
+and 2 side by side as one batch (every stage kernel is one launch over both
+runs), FP32 stepping with FP64 end-of-interval recovery.  Metric: grid-point-steps/s = runs * N^2 * RK4 steps / device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -319,9 +319,11 @@ def run_ours(args):
     N, n = w.N, w.n_steps
     prec = args.precision
     ic = np.ascontiguousarray(np.stack(w.initial_condition()))
-    streams = [torch.cuda.Stream() for _ in w.strategies]
+    stream = torch.cuda.Stream()
+    streams = [stream]
     params = lm.make_params(N, w.dt, precision=prec, f0=w.f0, c2=w.c2, nu8=w.nu8)
-    hs = [lm.sw_create(params, ic, s.cuda_stream) for s in streams]
+    hs = [lm.sw_create(params, ic, stream.cuda_stream) for _ in w.strategies]
+    batch = lm.sw_batch_create(hs)
     outs = [{k: torch.empty((N, N), dtype=torch.float64, device="cuda") for k in OUT_KEYS}
             for _ in hs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -331,12 +333,7 @@ def run_ours(args):
     def interval():
         for h, strat in zip(hs, w.strategies):
             lm.lmean_begin(h, lm.make_lm_params(strat, FIELDS, pos=True, eulerian=True, n_steps=n))
-        done = 0
-        while done < n:
-            c = min(chunk, n - done)
-            for h in hs:
-                lm.lmean_step(h, c)
-            done += c
+        lm.sw_batch_step(batch, n)
         for h, o in zip(hs, outs):
             lm.lmean_end(h, o)
 
@@ -360,7 +357,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    launches0 = sum(lm.sw_launch_count(h) for h in hs)
+    launches0 = lm.sw_batch_launch_count(batch) + sum(lm.sw_launch_count(h) for h in hs)
     clk = ClockSampler(local)
     clk.start()
     evs = []
@@ -371,7 +368,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
-    launches = sum(lm.sw_launch_count(h) for h in hs) - launches0
+    launches = lm.sw_batch_launch_count(batch) + sum(lm.sw_launch_count(h) for h in hs) - launches0
     ms = slowest_rank(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
     gp_per_step = len(hs) * N * N * n
     value = replica_throughput(gp_per_step * args.steps, world, ms * 1e-3)
@@ -415,12 +412,7 @@ def run_ours(args):
                 lm.sw_set_fields(h, ic_host)
             for h, strat in zip(hs, w.strategies):
                 lm.lmean_begin(h, lm.make_lm_params(strat, FIELDS, pos=True, eulerian=True, n_steps=n))
-            done = 0
-            while done < n:
-                c = min(chunk, n - done)
-                for h in hs:
-                    lm.lmean_step(h, c)
-                done += c
+            lm.sw_batch_step(batch, n)
             for h, o in zip(hs, host_out):
                 lm.lmean_end(h, o)
 
@@ -438,6 +430,7 @@ def run_ours(args):
                "d2h_bytes_per_step": len(hs) * len(OUT_KEYS) * N * N * 8,
                "note": "sw_set_fields from pinned host memory + interval + lmean_end to pinned host"}
 
+    lm.sw_batch_destroy(batch)
     for h in hs:
         lm.sw_destroy(h)
 

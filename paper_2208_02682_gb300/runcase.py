@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--graph-steps", type=int, default=16)
     ap.add_argument("--fields", default="zeta,h,u,v")
     ap.add_argument("--seed", type=int, default=1003)
+    ap.add_argument("--cufft", action="store_true",
+                    help="also time cuFFT (torch.fft) on the same transform counts, for comparison")
     args = ap.parse_args(argv)
 
     import torch
@@ -69,7 +71,40 @@ def main(argv=None):
                         "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9}
                     for k, (t, c, b) in sorted(kt.items(), key=lambda kv: -kv[1][0])},
     }
+    if args.cufft:
+        out["cufft_comparison"] = cufft_reference(torch, N, args.precision, kt)
     print(json.dumps(out))
+
+
+def cufft_reference(torch, N, precision, kt):
+    """cuFFT (through torch.fft, a library call timed only for comparison) on
+    the transforms one RK stage of Strategy 1 (zeta, h, u, v, positions)
+    performs: the row pass's complex N-point FFTs (N rows x 8 paired inverse
+    and 6 paired forward transforms) and the column passes' (K+1 columns x 16
+    inverse and 11 forward transforms).  Data movement and the physical-space
+    products of the stage kernels are not included."""
+    K = (N - 1) // 3
+    dt = torch.complex64 if precision == "f32" else torch.complex128
+    rows = torch.randn(14 * N, N, dtype=dt, device="cuda")
+    cols = torch.randn(27 * (K + 1), N, dtype=dt, device="cuda")
+    res = {}
+    for name, x in (("row_transforms", rows), ("column_transforms", cols)):
+        for _ in range(3):
+            torch.fft.fft(x, dim=1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            torch.fft.fft(x, dim=1)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / reps
+    res["note"] = "out-of-place batched C2C, data resident; the stage kernels also read, write and form products"
+    per = {k: t / c for k, (t, c, b) in kt.items()}
+    res["ours_row_prod_ms"] = per.get("row_prod")
+    res["ours_col_inv_plus_col_fwd_ms"] = per.get("col_inv", 0.0) + per.get("col_fwd", 0.0)
+    return res
 
 
 if __name__ == "__main__":
