@@ -35,9 +35,24 @@ template <typename T> __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { retu
 // multiply by i*k (spectral derivative)
 template <typename T> __device__ __forceinline__ cplx<T> cik(cplx<T> a, T k) { return mk<T>(-a.y * k, a.x * k); }
 
-// padded shared-memory index: one spare complex slot every 8 keeps the
-// stride-R writes of the first Stockham pass free of bank conflicts
-__host__ __device__ __forceinline__ int pad8(int n) { return n + (n >> 3); }
+// Shared-memory position of element n of a transform: one spare slot every
+// 8 elements.  Shared memory serves 8-byte accesses per half-warp from 16
+// slots of 8 bytes (16-byte accesses per quarter-warp from 8 slots); the
+// padding spreads the stride-8 writes of the first radix-8 pass over
+// distinct slots.  (An XOR swizzle that also keeps the consecutive accesses
+// conflict-free halves the shared-memory wavefronts of the FFT kernels but
+// costs more index arithmetic than it saves: the kernels are bound by
+// latency, not by shared-memory bandwidth.)
+template <typename T>
+__host__ __device__ __forceinline__ int sidx(int n) {
+  return n + (n >> 3);
+}
+// Distance between the transforms of a block (rows, or the columns of a
+// column tile).
+template <typename T>
+__host__ __device__ __forceinline__ int row_stride(int N) { return N + (N >> 3); }
+template <typename T>
+__host__ __device__ __forceinline__ int col_stride(int N, int C) { return N + (N >> 3); }
 
 // ---------------------------------------------------------------------------
 // Geometry of one grid

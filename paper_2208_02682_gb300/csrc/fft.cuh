@@ -11,11 +11,17 @@
 // length N runs with B*N/8 threads.  The pass reads all of its elements into
 // registers, synchronises, then writes in place.
 //
-// Transform b lives at buf + b*bstride, element n at pad8(n).  The twiddle
-// table holds tw[t] = exp(-2 pi i t / N), t < N (computed in FP64 on the host
-// and rounded to T); the inverse transform (sigma = +1) uses its conjugate.
-// No normalisation is applied.
+// Transform b lives at buf + b*bstride, element n at sidx<T>(n).  Twiddles come
+// from a pass-ordered table: the pass with stride Ns and radix R reads
+//   tw[r*Ns + k - 1] = exp(-2 pi i r k / (Ns R)),  1 <= r < R, 0 <= k < Ns,
+// (rows r of Ns consecutive entries; the index ranges of successive passes
+// tile [0, N-1)), so a warp's loads for one r are contiguous.  The table is
+// computed in FP64 on the host (fft_twiddle_table) and rounded to T; the
+// inverse transform (sigma = +1) uses its conjugate.  No normalisation.
 #pragma once
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 
 namespace lm {
@@ -52,44 +58,56 @@ __device__ __forceinline__ void dft8(cplx<T>* v) {
   v[3] = cadd<T>(a3, b3); v[7] = csub<T>(a3, b3);
 }
 
-// Twiddle exp(sigma 2 pi i e 2^tstep / N).  From the table (host FP64
-// values rounded to T), or, with TWC and FP32, from sincospif: that removes
-// the scattered table loads of the late passes, whose L1 wavefronts limit
-// kernels with many resident warps (the column passes); kernels with few
-// resident warps (the row passes) hide table loads better than the longer
-// sincospif chain.  The argument e 2^(tstep+1-log2N) is exact in FP32.
-template <typename T, int SIGN, bool TWC>
-__device__ __forceinline__ cplx<T> twiddle(int e, int tstep, int log2N, const cplx<T>* __restrict__ tw) {
-  cplx<T> t;
-  if (TWC && sizeof(T) == 4) {
-    float s, c;
-    sincospif(ldexpf((float)e, tstep + 1 - log2N), &s, &c);
-    t.x = (T)c;
-    t.y = (T)(-s);
-  } else {
-    t = __ldg(&tw[e << tstep]);
-  }
-  if (SIGN > 0) t.y = -t.y;
-  return t;
+// Pass sequence shared by the kernels (block_fft, group_fft) and the host
+// table builder: radix-8 passes, then one radix-4 or radix-2 pass for the
+// remaining bits.
+__host__ __device__ __forceinline__ int fft_num_passes(int log2N) { return (log2N + 2) / 3; }
+__host__ __device__ __forceinline__ int fft_pass_lr(int log2N, int p) {
+  return p < log2N / 3 ? 3 : log2N % 3;
 }
 
-// Twiddles w^{r k}, r < R, of one butterfly from three evaluations (w^k,
-// w^2k, w^4k); the others are products of those (at most two
-// multiplications deep).
+// Twiddles w^{r k}, 1 <= r < R, w = exp(sigma 2 pi i / (Ns R)), of one
+// butterfly.  FP64 loads all R - 1 from the table (FP64 multiplies are the
+// scarce resource).  FP32 evaluates w^k, w^2k, w^4k and forms the others as
+// products (at most two multiplications deep): from the table rows r = 1, 2,
+// 4, or, with TWC, from sincospif of 2 e / (Ns R) (exact in FP32) for e = k,
+// 2k, 4k; computed twiddles suit kernels with many resident warps whose table
+// loads would queue behind shared-memory traffic.
 template <typename T, int SIGN, int R, bool TWC>
-__device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int tstep, int log2N,
-                                                   const cplx<T>* __restrict__ tw) {
-  auto ld = [&](int e) { return twiddle<T, SIGN, TWC>(e, tstep, log2N, tw); };
-  w[1] = ld(k);
-  if (R >= 4) {
-    w[2] = ld(2 * k);
-    w[3] = cmul<T>(w[1], w[2]);
-  }
-  if (R == 8) {
-    w[4] = ld(4 * k);
-    w[5] = cmul<T>(w[4], w[1]);
-    w[6] = cmul<T>(w[4], w[2]);
-    w[7] = cmul<T>(w[4], w[3]);
+__device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int lNs, const cplx<T>* __restrict__ tw) {
+  constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  const cplx<T>* t = tw + (k - 1);
+  if (sizeof(T) == 4) {
+    auto ev = [&](int r) {
+      cplx<T> c;
+      if (TWC) {
+        float sn, cs;
+        sincospif(ldexpf((float)(r * k), 1 - lNs - LR), &sn, &cs);
+        c.x = (T)cs;
+        c.y = (T)(-sn);
+      } else {
+        c = __ldg(t + (r << lNs));
+      }
+      if (SIGN > 0) c.y = -c.y;
+      return c;
+    };
+    w[1] = ev(1);
+    if (R >= 4) {
+      w[2] = ev(2);
+      w[3] = cmul<T>(w[1], w[2]);
+    }
+    if (R == 8) {
+      w[4] = ev(4);
+      w[5] = cmul<T>(w[4], w[1]);
+      w[6] = cmul<T>(w[4], w[2]);
+      w[7] = cmul<T>(w[4], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      w[r] = __ldg(t + (r << lNs));
+      if (SIGN > 0) w[r].y = -w[r].y;
+    }
   }
 }
 
@@ -101,7 +119,6 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
   const int lNR = log2N - LR;
   const int NR = 1 << lNR;
   const int Ns = 1 << lNs;
-  const int tstep = log2N - lNs - LR;  // table index = (r*k) << tstep
   const int nthr = blockDim.x;
   cplx<T> v[8];
   int base[NB], outb[NB];
@@ -115,10 +132,10 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
     base[u] = b * bstride;
     outb[u] = ((j - k) << LR) + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[u * R + r] = src[pad8(j + r * NR)];
+    for (int r = 0; r < R; ++r) v[u * R + r] = src[sidx<T>(j + r * NR)];
     if (k > 0) {
       cplx<T> w[R];
-      butterfly_twiddles<T, SIGN, R, TWC>(w, k, tstep, log2N, tw);
+      butterfly_twiddles<T, SIGN, R, TWC>(w, k, lNs, tw);
 #pragma unroll
       for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], w[r]);
     }
@@ -137,7 +154,7 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int log2N, int lNs, 
       vv[1] = csub<T>(a, b);
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) buf[base[u] + pad8(outb[u] + q * Ns)] = vv[q];
+    for (int q = 0; q < R; ++q) buf[base[u] + sidx<T>(outb[u] + q * Ns)] = vv[q];
   }
   __syncthreads();
 }
@@ -157,6 +174,118 @@ __device__ void block_fft(cplx<T>* buf, int log2N, int bstride, const cplx<T>* _
   }
   if (rem == 2) stockham_pass<T, SIGN, 2, TWC>(buf, log2N, lNs, bstride, tw);
   if (rem == 1) stockham_pass<T, SIGN, 1, TWC>(buf, log2N, lNs, bstride, tw);
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident transforms owned by a group of G = N/8 threads (one
+// transform per group; groups never wait for one another).  Thread j of the
+// group holds elements j + m G, m < 8, of its transform in x[m] on entry
+// (input) and on exit (output): the first pass's butterflies read exactly
+// these positions, and the last pass's butterflies write them.  The passes in
+// between exchange through two shared buffers used alternately, so each pass
+// costs one group barrier.  `w` selects the buffer that is free to write; the
+// function leaves it pointing at the buffer not read last.
+
+// Barrier over the group's G threads: the warp when G <= 32 (several groups
+// per warp execute the same instructions), else named barrier 1 + grp.
+__device__ __forceinline__ void group_sync(int G, int grp) {
+  if (G <= 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(G) : "memory");
+}
+
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void dft_r(cplx<T>* v) {
+  if (R == 8) {
+    dft8<T, SIGN>(v);
+  } else if (R == 4) {
+    dft4<T, SIGN>(v[0], v[1], v[2], v[3]);
+  } else {
+    const cplx<T> a = v[0], b = v[1];
+    v[0] = cadd<T>(a, b);
+    v[1] = csub<T>(a, b);
+  }
+}
+
+// One Stockham pass of a group transform, from shared memory `in` to shared
+// memory `out` (or, LAST, to the output registers x).
+template <typename T, int SIGN, int LR, bool LAST, bool TWC>
+__device__ __forceinline__ void group_pass(cplx<T>* x, const cplx<T>* in, cplx<T>* out, int j, int G, int lNs,
+                                           const cplx<T>* __restrict__ tw) {
+  constexpr int R = 1 << LR;
+  constexpr int NB = 8 / R;
+  const int NR = G * NB;
+  const int Ns = 1 << lNs;
+  cplx<T> v[8];
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int jj = u * G + j;
+    const int k = jj & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[u * R + r] = in[sidx<T>(jj + r * NR)];
+    if (k > 0) {
+      cplx<T> wr[R];
+      butterfly_twiddles<T, SIGN, R, TWC>(wr, k, lNs, tw);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], wr[r]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    dft_r<T, SIGN, R>(v + u * R);
+    const int jj = u * G + j;
+    const int k = jj & (Ns - 1);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (LAST) x[u + q * NB] = v[u * R + q];
+      else out[sidx<T>(((jj - k) << LR) + k + q * Ns)] = v[u * R + q];
+    }
+  }
+}
+
+template <typename T, int SIGN, bool TWC = false>
+__device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int G, int grp, int log2N,
+                          const cplx<T>* __restrict__ tw) {
+  // first pass: radix 8, stride 1, no twiddles; butterfly j takes x[0..7]
+  dft8<T, SIGN>(x);
+  {
+    cplx<T>* out = w ? buf1 : buf0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[sidx<T>((j << 3) + q)] = x[q];
+  }
+  group_sync(G, grp);
+  // radix-8 passes, then the last pass (radix 8, 4 or 2) into the registers
+  const int np = fft_num_passes(log2N);
+  int lNs = 3;
+  for (int p = 1; p < np - 1; ++p) {
+    group_pass<T, SIGN, 3, false, TWC>(x, w ? buf1 : buf0, w ? buf0 : buf1, j, G, lNs, tw);
+    group_sync(G, grp);
+    w ^= 1;
+    lNs += 3;
+  }
+  const cplx<T>* in = w ? buf1 : buf0;
+  const int lr = fft_pass_lr(log2N, np - 1);
+  if (lr == 3) group_pass<T, SIGN, 3, true, TWC>(x, in, nullptr, j, G, lNs, tw);
+  else if (lr == 2) group_pass<T, SIGN, 2, true, TWC>(x, in, nullptr, j, G, lNs, tw);
+  else group_pass<T, SIGN, 1, true, TWC>(x, in, nullptr, j, G, lNs, tw);
+  w ^= 1;
+}
+
+// Host: the pass-ordered twiddle table of an N-point transform (N - 1
+// entries, FP64).
+inline void fft_twiddle_table(int log2N, double* re, double* im) {
+  const double twopi = 6.283185307179586476925286766559;
+  int lNs = 0;
+  for (int p = 0; p < fft_num_passes(log2N); ++p) {
+    const int lr = fft_pass_lr(log2N, p);
+    const int Ns = 1 << lNs, R = 1 << lr;
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
+        const double a = twopi * (double)(r * k) / (double)(Ns * R);
+        re[r * Ns + k - 1] = std::cos(a);
+        im[r * Ns + k - 1] = -std::sin(a);
+      }
+    lNs += lr;
+  }
 }
 
 }  // namespace lm

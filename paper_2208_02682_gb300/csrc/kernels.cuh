@@ -18,7 +18,7 @@ namespace lm {
 
 // ---------------------------------------------------------------------------
 // Column passes on a tile of C = 2^lC consecutive kx columns (kx0 a multiple
-// of C, KXP a multiple of C), C*N/8 threads, smem C*pad8(N) complex.  The
+// of C, KXP a multiple of C), C*N/8 threads, smem C*col_stride(N, C) complex.  The
 // tile's global accesses are C-wide contiguous runs along kx.
 
 // inverse: d = IFFT_y(op(s1[, s2])), op in {id, d_x, d_y, curl}, zero-padded
@@ -28,7 +28,7 @@ __device__ void col_inverse_tile(cplx<T>* buf, const cplx<T>* __restrict__ s1, c
                                  int op, cplx<T>* __restrict__ d, const Geom& g, int lC, int kx0,
                                  const cplx<T>* __restrict__ tw) {
   const int N = g.N, K = g.K, KXP = g.KXP;
-  const int C = 1 << lC, bst = pad8(N);
+  const int C = 1 << lC, bst = col_stride<T>(N, C);
   const int nthr = blockDim.x, tid = threadIdx.x;
   // every element written once: op(S) at n = ky mod N for |ky| <= K, else 0
   for (int e = tid; e < N * C; e += nthr) {
@@ -47,13 +47,13 @@ __device__ void col_inverse_tile(cplx<T>* buf, const cplx<T>* __restrict__ s1, c
         v = csub<T>(cik<T>(y, (T)kx), cik<T>(x, (T)ky));
       }
     }
-    buf[c * bst + pad8(n)] = v;
+    buf[c * bst + sidx<T>(n)] = v;
   }
   __syncthreads();
   block_fft<T, +1, true>(buf, g.log2N, bst, tw);
   for (int e = tid; e < N * C; e += nthr) {
     const int n = e >> lC, c = e & (C - 1);
-    d[(long long)n * KXP + kx0 + c] = buf[c * bst + pad8(n)];
+    d[(long long)n * KXP + kx0 + c] = buf[c * bst + sidx<T>(n)];
   }
 }
 
@@ -62,11 +62,11 @@ template <typename T>
 __device__ void col_forward_tile(cplx<T>* buf, const cplx<T>* __restrict__ s, cplx<T>* __restrict__ d,
                                  const Geom& g, int lC, int kx0, const cplx<T>* __restrict__ tw) {
   const int N = g.N, K = g.K, KXP = g.KXP;
-  const int C = 1 << lC, bst = pad8(N);
+  const int C = 1 << lC, bst = col_stride<T>(N, C);
   const int nthr = blockDim.x, tid = threadIdx.x;
   for (int e = tid; e < N * C; e += nthr) {
     const int n = e >> lC, c = e & (C - 1);
-    buf[c * bst + pad8(n)] = s[(long long)n * KXP + kx0 + c];
+    buf[c * bst + sidx<T>(n)] = s[(long long)n * KXP + kx0 + c];
   }
   __syncthreads();
   block_fft<T, -1, true>(buf, g.log2N, bst, tw);
@@ -76,7 +76,7 @@ __device__ void col_forward_tile(cplx<T>* buf, const cplx<T>* __restrict__ s, cp
     const int kx = kx0 + c;
     const int ky = kyi - K;
     cplx<T> v = mk<T>(0, 0);
-    if (kx <= K) v = cscale<T>(buf[c * bst + pad8(ky & (N - 1))], inv);
+    if (kx <= K) v = cscale<T>(buf[c * bst + sidx<T>(ky & (N - 1))], inv);
     d[(long long)kyi * KXP + kx] = v;
   }
 }
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const __grid_constant__ ColFwd
 
 // ---------------------------------------------------------------------------
 // Row helpers.  A block owns B consecutive rows; its FFT buffer holds B
-// transforms of length N at stride pad8(N).
+// transforms of length N at stride row_stride(N).
 
 // Fill buf with the Hermitian-paired spectrum Z = A + iB of two real rows
 // whose kx >= 0 halves are mixed fields a and b (b < 0: zero), then inverse
@@ -134,7 +134,7 @@ __device__ void row_pair_inverse(cplx<T>* buf, const cplx<T>* __restrict__ ma,
                                  const cplx<T>* __restrict__ mb, int row0, int B,
                                  const Geom& g, const cplx<T>* __restrict__ tw) {
   const int N = g.N, K = g.K, KXP = g.KXP;
-  const int bst = pad8(N);
+  const int bst = row_stride<T>(N);
   const int nthr = blockDim.x, tid = threadIdx.x;
   // Z(k) = A + iB and Z(N-k) = conj(A) + i conj(B) for k <= K (each input
   // read once); the band K < n < N-K is zeroed.  The two writes never touch
@@ -142,7 +142,7 @@ __device__ void row_pair_inverse(cplx<T>* buf, const cplx<T>* __restrict__ ma,
   const int nz = N - 2 * K - 1;
   for (int e = tid; e < B * nz; e += nthr) {
     const int r = e / nz, n = K + 1 + (e - r * nz);
-    buf[r * bst + pad8(n)] = mk<T>(0, 0);
+    buf[r * bst + sidx<T>(n)] = mk<T>(0, 0);
   }
   for (int e = tid; e < B * (K + 1); e += nthr) {
     const int r = e / (K + 1), k = e - r * (K + 1);
@@ -153,8 +153,8 @@ __device__ void row_pair_inverse(cplx<T>* buf, const cplx<T>* __restrict__ ma,
     if (k == 0) {
       z[0] = mk<T>(A.x, Bv.x);
     } else {
-      z[pad8(k)] = mk<T>(A.x - Bv.y, A.y + Bv.x);
-      z[pad8(N - k)] = mk<T>(A.x + Bv.y, -A.y + Bv.x);
+      z[sidx<T>(k)] = mk<T>(A.x - Bv.y, A.y + Bv.x);
+      z[sidx<T>(N - k)] = mk<T>(A.x + Bv.y, -A.y + Bv.x);
     }
   }
   __syncthreads();
@@ -168,7 +168,7 @@ __device__ void row_pair_forward_store(cplx<T>* buf, cplx<T>* __restrict__ da,
                                        cplx<T>* __restrict__ db, int row0, int B,
                                        const Geom& g, const cplx<T>* __restrict__ tw) {
   const int N = g.N, K = g.K, KXP = g.KXP;
-  const int bst = pad8(N);
+  const int bst = row_stride<T>(N);
   const int nthr = blockDim.x, tid = threadIdx.x;
   __syncthreads();
   block_fft<T, -1>(buf, g.log2N, bst, tw);
@@ -178,8 +178,8 @@ __device__ void row_pair_forward_store(cplx<T>* buf, cplx<T>* __restrict__ da,
     const cplx<T>* z = buf + r * bst;
     cplx<T> P = mk<T>(0, 0), Q = mk<T>(0, 0);
     if (k <= K) {
-      cplx<T> z1 = z[pad8(k)];
-      cplx<T> z2 = z[pad8((N - k) & (N - 1))];
+      cplx<T> z1 = z[sidx<T>(k)];
+      cplx<T> z2 = z[sidx<T>((N - k) & (N - 1))];
       // P = (Z(k) + conj Z(N-k))/2, Q = (Z(k) - conj Z(N-k))/(2i)
       P = mk<T>((z1.x + z2.x) * h, (z1.y - z2.y) * h);
       Q = mk<T>((z1.y + z2.y) * h, (z2.x - z1.x) * h);
@@ -189,6 +189,61 @@ __device__ void row_pair_forward_store(cplx<T>* buf, cplx<T>* __restrict__ da,
     if (db) db[off] = Q;
   }
   __syncthreads();
+}
+
+// Group-owned row transforms (one row per group of G = N/8 threads; thread
+// j holds positions j + m G, see group_fft).
+
+// Hermitian-paired spectrum of one row of mixed fields a and b at the
+// thread's positions k = j + m G: Z(k) = A(k) + i B(k) for k <= K,
+// conj A(N-k) + i conj B(N-k) for k >= N-K, zero in between; the kx = 0
+// imaginary parts are dropped, as a real inverse transform does.
+template <typename T>
+__device__ __forceinline__ void load_pair_spectrum(cplx<T> (&x)[8], const cplx<T>* __restrict__ ma,
+                                                   const cplx<T>* __restrict__ mb, long long rowoff, int j, int G,
+                                                   int N, int K) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = j + m * G;
+    cplx<T> z = mk<T>(0, 0);
+    if (k <= K) {
+      const cplx<T> A = ma[rowoff + k];
+      const cplx<T> Bv = mb ? mb[rowoff + k] : mk<T>(0, 0);
+      z = k == 0 ? mk<T>(A.x, Bv.x) : mk<T>(A.x - Bv.y, A.y + Bv.x);
+    } else if (k >= N - K) {
+      const cplx<T> A = ma[rowoff + (N - k)];
+      const cplx<T> Bv = mb ? mb[rowoff + (N - k)] : mk<T>(0, 0);
+      z = mk<T>(A.x + Bv.y, -A.y + Bv.x);
+    }
+    x[m] = z;
+  }
+}
+
+// Spectrum Z of p + i q held at the thread's positions -> kx in [0, KXP)
+// halves of p and q, scaled by 1/N, into row `rowoff` of mixed fields da and
+// db (db null: p only).  One exchange through the free buffer.
+template <typename T>
+__device__ __forceinline__ void store_pair_spectrum(const cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
+                                                    cplx<T>* __restrict__ da, cplx<T>* __restrict__ db,
+                                                    long long rowoff, int j, int G, int grp, int N, int K, int KXP) {
+  cplx<T>* b = w ? buf1 : buf0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) b[sidx<T>(j + m * G)] = x[m];
+  group_sync(G, grp);
+  const T h = (T)0.5 / (T)N;
+  for (int k = j; k < KXP; k += G) {
+    cplx<T> P = mk<T>(0, 0), Q = mk<T>(0, 0);
+    if (k <= K) {
+      const cplx<T> z1 = b[sidx<T>(k)];
+      const cplx<T> z2 = b[sidx<T>((N - k) & (N - 1))];
+      // P = (Z(k) + conj Z(N-k))/2, Q = (Z(k) - conj Z(N-k))/(2i)
+      P = mk<T>((z1.x + z2.x) * h, (z1.y - z2.y) * h);
+      Q = mk<T>((z1.y + z2.y) * h, (z2.x - z1.x) * h);
+    }
+    da[rowoff + k] = P;
+    if (db) db[rowoff + k] = Q;
+  }
+  w ^= 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -227,7 +282,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const __grid_constant__ RowInvA
     for (int e = tid; e < B * N; e += nthr) {
       const int r = e / N, x = e - r * N;
       const int y = row0 + r;
-      const cplx<T> v = buf[r * (pad8(N)) + pad8(x)];
+      const cplx<T> v = buf[r * row_stride<T>(N) + sidx<T>(x)];
       const long long off = (long long)y * N + x;
       if (a.oa[p] >= 0)
         a.dst[a.oa[p] * a.dst_stride + off] =
@@ -267,7 +322,7 @@ __global__ void __launch_bounds__(256) k_row_fwd(const __grid_constant__ RowFwdA
     for (int e = tid; e < B * N; e += nthr) {
       const int r = e / N, x = e - r * N;
       const long long off = (long long)(row0 + r) * N + x;
-      buf[r * pad8(N) + pad8(x)] = mk<T>((T)pa[off], pb ? (T)pb[off] : (T)0);
+      buf[r * row_stride<T>(N) + sidx<T>(x)] = mk<T>((T)pa[off], pb ? (T)pb[off] : (T)0);
     }
     row_pair_forward_store<T>(buf, a.dst + (long long)a.oa[p] * g.mi,
                               a.ob[p] >= 0 ? a.dst + (long long)a.ob[p] * g.mi : nullptr,

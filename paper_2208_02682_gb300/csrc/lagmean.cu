@@ -325,8 +325,9 @@ static int batch_build_t(BatchExec* b) {
     const RunDesc<T>& d = descs[r];
     const int N = h->g.N;
     const int thr[KT_COUNT] = {((1 << h->lC) * N) / 8, h->Bi * N / 8, 256, h->Bp * N / 8, ((1 << h->lC) * N) / 8, 256};
-    const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * pad8(N) * cs, (size_t)h->Bi * pad8(N) * cs, 0,
-                                 row_prod_smem<T>(N, h->Bp, h->L.strategy), (size_t)(1 << h->lC) * pad8(N) * cs, 0};
+    const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * col_stride<T>(N, 1 << h->lC) * cs,
+                                 (size_t)2 * h->Bi * row_stride<T>(N) * cs, 0, row_prod_smem<T>(N, h->Bp, h->L.strategy),
+                                 (size_t)(1 << h->lC) * col_stride<T>(N, 1 << h->lC) * cs, 0};
     const KBytes kb = kernel_bytes(h, h->L);
     const double by[KT_COUNT] = {kb.col_inv, kb.row_inv, kb.phys_q, kb.row_prod, kb.col_fwd, 0.0};
     for (int k = 0; k < KT_COUNT; ++k) {
@@ -695,11 +696,11 @@ static void host_tables(const sw_params& p, const Geom& g, void* ef_host, void* 
       ef[m] = (T)std::exp(-p.nu8 * k8 * p.dt * 0.5);
       ef[g.ms + m] = (T)std::exp(-p.lm_nu8 * k8 * p.dt * 0.5);
     }
-  const double twopi = 6.283185307179586476925286766559;
+  std::vector<double> re(g.N, 1.0), im(g.N, 0.0);
+  fft_twiddle_table(g.log2N, re.data(), im.data());
   for (int t = 0; t < g.N; ++t) {
-    const double a = twopi * (double)t / (double)g.N;
-    tw64_host[t] = make_double2(std::cos(a), -std::sin(a));
-    tw[t] = mk<T>((T)std::cos(a), (T)(-std::sin(a)));
+    tw64_host[t] = make_double2(re[t], im[t]);
+    tw[t] = mk<T>((T)re[t], (T)im[t]);
   }
 }
 

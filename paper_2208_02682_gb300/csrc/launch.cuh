@@ -16,7 +16,7 @@ inline int row_block_rows(int N, int points = 512) {
 }
 
 template <typename T> size_t row_prod_smem(int N, int B, int strategy) {
-  return (size_t)2 * B * pad8(N) * sizeof(cplx<T>) + (size_t)(strategy == 2 ? 6 : 4) * B * N * sizeof(T);
+  return (size_t)B * (2 * row_stride<T>(N) * sizeof(cplx<T>) + (size_t)(strategy == 2 ? 9 : 6) * N * sizeof(T));
 }
 
 template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStream_t s);
@@ -62,27 +62,27 @@ template <typename T> static cudaError_t prepare_kernels_t() {
 }
 
 template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStream_t s) {
-  const size_t sm = (size_t)4 * pad8(a.g.N) * sizeof(cplx<T>);
+  const size_t sm = (size_t)4 * col_stride<T>(a.g.N, 4) * sizeof(cplx<T>);
   dim3 grid(a.g.KXP / 4, a.nout);
   k_col_inv<T><<<grid, a.g.N / 2, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T> cudaError_t launch_col_fwd(const ColFwdArgs<T>& a, cudaStream_t s) {
-  const size_t sm = (size_t)4 * pad8(a.g.N) * sizeof(cplx<T>);
+  const size_t sm = (size_t)4 * col_stride<T>(a.g.N, 4) * sizeof(cplx<T>);
   dim3 grid(a.g.KXP / 4, a.nout);
   k_col_fwd<T><<<grid, a.g.N / 2, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, typename TO> cudaError_t launch_row_inv(const RowInvArgs<T, TO>& a, cudaStream_t s) {
-  const size_t sm = (size_t)a.B * pad8(a.g.N) * sizeof(cplx<T>);
+  const size_t sm = (size_t)a.B * row_stride<T>(a.g.N) * sizeof(cplx<T>);
   k_row_inv<T, TO><<<a.g.N / a.B, a.B * a.g.N / 8, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s) {
-  const size_t sm = (size_t)a.B * pad8(a.g.N) * sizeof(cplx<T>);
+  const size_t sm = (size_t)a.B * row_stride<T>(a.g.N) * sizeof(cplx<T>);
   k_row_fwd<T><<<a.g.N / a.B, a.B * a.g.N / 8, sm, s>>>(a);
   return cudaGetLastError();
 }

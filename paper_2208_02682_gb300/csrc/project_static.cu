@@ -25,12 +25,20 @@ void set_handleless_error(const std::string& msg);
 // holds it until the process exits.
 static __device__ __align__(256) unsigned char g_project_scratch[SW_PROJECT_STATIC_BYTES];
 
-// Twiddles exp(-2 pi i t/N), t < N, in FP64.
-__global__ void k_static_twiddles(double2* tw, int N) {
+// The pass-ordered FP64 twiddle table of the N-point transforms (entry
+// r*Ns + k - 1 of the pass with stride Ns and radix R: exp(-2 pi i r k/(Ns R))).
+__global__ void k_static_twiddles(double2* tw, int N, int log2N) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < N) {
+  if (t < N - 1) {
+    // the pass whose index range [Ns - 1, Ns R - 1) holds t
+    int lNs = 0, lr = fft_pass_lr(log2N, 0);
+    for (int p = 1; p < fft_num_passes(log2N) && t + 1 >= (1 << (lNs + lr)); ++p) {
+      lNs += lr;
+      lr = fft_pass_lr(log2N, p);
+    }
+    const int r = (t + 1) >> lNs, k = (t + 1) & ((1 << lNs) - 1);
     double s, c;
-    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    sincospi(2.0 * (double)(r * k) / (double)(1 << (lNs + lr)), &s, &c);
     tw[t] = make_double2(c, -s);
   }
 }
@@ -112,7 +120,7 @@ extern "C" int sw_project_static(const double* in, double* out, int N, void* str
   double2* tw = (double2*)((char*)base + o_tw);
   cudaStream_t s = (cudaStream_t)stream;
 
-  k_static_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+  k_static_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N, g.log2N);
   cudaError_t e = cudaGetLastError();
   const int B = row_block_rows(N);
   if (e == cudaSuccess) {

@@ -108,28 +108,35 @@ __global__ void __launch_bounds__(1024) k_stage_col_fwd(const RunDesc<T>* __rest
 }
 
 // a3: Strategy-2 gather buffer (physical u, v | h, zeta), local block =
-// (pair, row block).
+// (pair, row block of Bi rows, one row per group of N/8 threads).
 template <typename T>
 __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restrict__ runs,
                                                        const int* __restrict__ start, int nruns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   const Geom& g = d.g;
+  const int N = g.N, G = N >> 3, B = d.Bi;
   const int lb = blockIdx.x - start[r];
-  const int nrb = g.N / d.Bi;
+  const int nrb = N / B;
   const int pair = lb / nrb, rb = lb - pair * nrb;
-  const int B = d.Bi, N = g.N, row0 = rb * B;
+  const int grp = threadIdx.x / G, j = threadIdx.x - grp * G;
+  const int y = rb * B + grp;
+  const int rs = row_stride<T>(N);
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
+  cplx<T>* buf1 = buf0 + rs;
   const int ia = pair == 0 ? d.L.i_u : d.L.i_h, ib = pair == 0 ? d.L.i_v : d.L.i_z;
   const int oa = pair == 0 ? PH_U : PH_H, ob = pair == 0 ? PH_V : PH_Z;
-  row_pair_inverse<T>(buf, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, row0, B, g, d.tw);
-  for (int e = threadIdx.x; e < B * N; e += blockDim.x) {
-    const int rr = e >> g.log2N, x = e & (N - 1);
-    const cplx<T> v = buf[rr * pad8(N) + pad8(x)];
-    const long long off = (long long)(row0 + rr) * N + x;
-    d.phys[oa * g.np + off] = v.x;
-    d.phys[ob * g.np + off] = v.y;
+  cplx<T> x[8];
+  int w = 0;
+  load_pair_spectrum<T>(x, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, (long long)y * g.KXP, j, G, N,
+                        g.K);
+  group_fft<T, +1>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const long long off = (long long)y * N + j + m * G;
+    d.phys[oa * g.np + off] = x[m].x;
+    d.phys[ob * g.np + off] = x[m].y;
   }
 }
 
@@ -146,32 +153,40 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 }
 
 // ---------------------------------------------------------------------------
-// a2: row pass with products.  Local block = (pair group, row block): Bp rows
-// and product pairs [grp*ppb, (grp+1)*ppb).  Smem: W, P (Bp*pad8(N) complex
-// each), U (4*Bp*N reals: u, v, h, zeta), XI (2*Bp*N reals, Strategy 2).
+// a2: row pass with products.  Local block = (pair group, row block): Bp rows,
+// one per group of G = N/8 threads, and product pairs [grp*ppb,
+// (grp+1)*ppb).  Every transform stays in the registers of its group
+// (group_fft): a row's physical values live at the thread's own positions
+// x = j + m G, where the products are formed and the forward transform of
+// each product pair starts.  Smem per group: two exchange buffers of
+// row_stride(N) complex, then U (u, v, h, zeta), for Strategy 2 XI (xi_x,
+// xi_y) and S (gathered values), and PZ (the two products of a pair), N
+// reals each, read back only by the thread that wrote them.
 template <typename T>
-__global__ void __launch_bounds__(256) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
                                                         const int* __restrict__ start, int nruns, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   const Geom& g = d.g;
   const Layout& L = d.L;
-  const int N = g.N, B = d.Bp;
-  const int bst = pad8(N);
+  const int N = g.N, B = d.Bp, G = N >> 3;
   const int lb = blockIdx.x - start[r];
   const int nrb = N / B;
-  const int grp = lb / nrb, rb = lb - grp * nrb;
-  cplx<T>* W = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* P = W + B * bst;
-  T* U = reinterpret_cast<T*>(P + B * bst);
-  T* XI = U + 4 * B * N;
-  const int row0 = rb * B;
+  const int pg = lb / nrb, rb = lb - pg * nrb;
+  const int grp = threadIdx.x / G, j = threadIdx.x - grp * G;
+  const int y = rb * B + grp;
+  const int rs = row_stride<T>(N);
+  const int nu = L.strategy == 2 ? 7 : 4;  // + 2 for PZ
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
+  cplx<T>* buf1 = buf0 + rs;
+  T* U = reinterpret_cast<T*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)B * 2 * rs) + (size_t)grp * (nu + 2) * N;
+  T* XI = U + 4 * N;
+  T* S = U + 6 * N;
+  T* PZ = U + nu * N;
   const int np = L.np;
-  const int p0 = grp * d.ppb * 2;
+  const int p0 = pg * d.ppb * 2;
   const int p1 = min(np, p0 + d.ppb * 2);
-  const int nthr = blockDim.x, tid = threadIdx.x;
-  const int BN = B * N;
   const bool kin = L.model == 1;
   const T adv_x = (T)d.c.adv_x, adv_y = (T)d.c.adv_y;
   const T f0 = (T)d.c.f0;
@@ -180,6 +195,8 @@ __global__ void __launch_bounds__(256) k_stage_row_prod(const RunDesc<T>* __rest
   const T inv_s = s0 ? (T)0 : (T)(1.0 / s);
   const T inv_dx = (T)((double)N / 6.283185307179586476925286766559);
   const cplx<T>* mix = d.mix;
+  const long long rowoff = (long long)y * g.KXP;
+  int w = 0;
 
   // which physical base fields this block's products read
   bool need_uv = false, need_hz = false;
@@ -189,108 +206,136 @@ __global__ void __launch_bounds__(256) k_stage_row_prod(const RunDesc<T>* __rest
     if (k == PK_ZV || k == PK_ZU || k == PK_KE || k == PK_HU || k == PK_HV) need_uv = true;
     if ((k == PK_ADV || k == PK_XI || k == PK_GBAR) && !kin) need_uv = true;
   }
-  // physical u, v, h, zeta (and xi) of the block's rows
+  // Inverse steps before the products: base pairs into U (and XI).  Strategy
+  // 2 reads u, v, h, zeta from the gather buffer and transforms xi only.
+  int base_a[2], base_b[2], base_o[2];
+  int nbase = 0;
   if (L.strategy == 2) {
-    for (int e = tid; e < BN; e += nthr) {
-      const long long off = (long long)row0 * N + e;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) U[f * BN + e] = d.phys[f * g.np + off];
+    for (int m = 0; m < 8; ++m) {
+      const long long off = (long long)y * N + j + m * G;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) U[f * N + m * G + j] = d.phys[f * g.np + off];
     }
-    row_pair_inverse<T>(W, mix + (long long)L.i_xi[0] * g.mi, mix + (long long)L.i_xi[1] * g.mi, row0, B, g,
-                        d.tw);
-    for (int e = tid; e < BN; e += nthr) {
-      const int rr = e >> g.log2N, x = e & (N - 1);
-      const cplx<T> v = W[rr * bst + pad8(x)];
-      XI[e] = v.x;
-      XI[BN + e] = v.y;
-    }
+    base_a[0] = L.i_xi[0], base_b[0] = L.i_xi[1], base_o[0] = 4;
+    nbase = 1;
   } else {
-    if (need_uv) {
-      row_pair_inverse<T>(W, mix + (long long)L.i_u * g.mi, mix + (long long)L.i_v * g.mi, row0, B, g, d.tw);
-      for (int e = tid; e < BN; e += nthr) {
-        const int rr = e >> g.log2N, x = e & (N - 1);
-        const cplx<T> v = W[rr * bst + pad8(x)];
-        U[e] = v.x;
-        U[BN + e] = v.y;
-      }
-      __syncthreads();
-    }
-    if (need_hz) {
-      row_pair_inverse<T>(W, mix + (long long)L.i_h * g.mi, mix + (long long)L.i_z * g.mi, row0, B, g, d.tw);
-      for (int e = tid; e < BN; e += nthr) {
-        const int rr = e >> g.log2N, x = e & (N - 1);
-        const cplx<T> v = W[rr * bst + pad8(x)];
-        U[2 * BN + e] = v.x;
-        U[3 * BN + e] = v.y;
-      }
-    }
+    if (need_uv) base_a[nbase] = L.i_u, base_b[nbase] = L.i_v, base_o[nbase] = 0, ++nbase;
+    if (need_hz) base_a[nbase] = L.i_h, base_b[nbase] = L.i_z, base_o[nbase] = 2, ++nbase;
   }
-  __syncthreads();
 
-  // products, two at a time through the forward FFT
-  int slot = 0;
-  int pend = -1;
-  for (int p = p0; p < p1; ++p) {
-    const int kind = L.pk[p];
-    const bool need_grad = kind == PK_ADV || kind == PK_XI || kind == PK_GBAR;
-    if (need_grad)
-      row_pair_inverse<T>(W, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, row0, B, g, d.tw);
+  // One loop over the inverse steps and the products, so that each direction
+  // of the group transform is instantiated once.
+  cplx<T> x[8];
+  int slot = 0, pend = -1;
+  int t = 0, p = p0;
+  while (t < nbase || p < p1) {
+    const bool is_base = t < nbase;
+    const int kind = is_base ? -1 : L.pk[p];
+    const bool need_inv = is_base || kind == PK_ADV || kind == PK_XI || kind == PK_GBAR;
+    if (need_inv) {
+      const int ia = is_base ? base_a[t] : L.pa[p], ib = is_base ? base_b[t] : L.pb[p];
+      load_pair_spectrum<T>(x, mix + (long long)ia * g.mi, mix + (long long)ib * g.mi, rowoff, j, G, N, g.K);
+      group_fft<T, +1>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
+    }
+    if (is_base) {
+      T* dst = U + base_o[t] * N;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        dst[m * G + j] = x[m].x;
+        dst[N + m * G + j] = x[m].y;
+      }
+      ++t;
+      continue;
+    }
     const int pc = L.pc[p];
-    for (int e = tid; e < BN; e += nthr) {
-      const int rr = e >> g.log2N, x = e & (N - 1);
-      const T u = U[e], v = U[BN + e], h = U[2 * BN + e], z = U[3 * BN + e];
-      T val;
-      switch (kind) {
-        case PK_ZV: val = z * v; break;
-        case PK_ZU: val = z * u; break;
-        case PK_KE: val = (T)0.5 * (u * u + v * v); break;
-        // depth h = 1 + eta; the state and the row buffers hold eta
-        case PK_HU: val = u + h * u; break;
-        case PK_HV: val = v + h * v; break;
-        case PK_Q: val = (f0 + z) / ((T)1 + h); break;
-        case PK_ADV: {
-          // u.grad G (Eq. gtilde-evol) or u.grad D
-          const cplx<T> dd = W[rr * bst + pad8(x)];
-          const T ua = kin ? adv_x : u, va = kin ? adv_y : v;
-          val = ua * dd.x + va * dd.y;
-          break;
+    // value of this product at position m: slot `slot` of the pair in PZ
+    T* const pz = PZ + slot * N;
+    auto put = [&](int m, T v) { pz[m * G + j] = v; };
+    switch (kind) {
+      case PK_ZV:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[N + m * G + j]);
+        break;
+      case PK_ZU:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[m * G + j]);
+        break;
+      case PK_KE:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T u = U[m * G + j], v = U[N + m * G + j];
+          put(m, (T)0.5 * (u * u + v * v));
         }
-        default: {
-          // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0
-          const cplx<T> dd = W[rr * bst + pad8(x)];
-          const T xx = XI[e], xy = XI[BN + e];
-          const T ua = kin ? adv_x : u, va = kin ? adv_y : v;
+        break;
+      // depth h = 1 + eta; the state and the row buffers hold eta
+      case PK_HU:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T u = U[m * G + j];
+          put(m, u + U[2 * N + m * G + j] * u);
+        }
+        break;
+      case PK_HV:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T v = U[N + m * G + j];
+          put(m, v + U[2 * N + m * G + j] * v);
+        }
+        break;
+      case PK_Q:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, (f0 + U[3 * N + m * G + j]) / ((T)1 + U[2 * N + m * G + j]));
+        break;
+      case PK_ADV:
+        // u.grad G (Eq. gtilde-evol) or u.grad D
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T ua = kin ? adv_x : U[m * G + j], va = kin ? adv_y : U[N + m * G + j];
+          put(m, ua * x[m].x + va * x[m].y);
+        }
+        break;
+      default: {
+        // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0.
+        // The gathered values go through the thread's own slots of S first,
+        // so that only a few of the bilinear loads are in flight per thread.
+#pragma unroll 1
+        for (int m = 0; m < 8; ++m) {
+          const int e = m * G + j;
+          const T xx = XI[e], xy = XI[N + e];
+          T fi;
+          if (kind == PK_XI && kin) fi = pc == 0 ? adv_x : adv_y;
+          else fi = bilinear<T>(d.phys + (long long)pc * g.np, e, y, xx, xy, inv_dx, N);
+          S[e] = fi;
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int e = m * G + j;
+          const T xx = XI[e], xy = XI[N + e];
+          const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
           const T wx = s0 ? (T)0.5 * ua : xx * inv_s;
           const T wy = s0 ? (T)0.5 * va : xy * inv_s;
-          const T wg = wx * dd.x + wy * dd.y;
-          const int yy = row0 + rr;
-          if (kind == PK_XI) {
-            T ui;
-            if (kin) ui = pc == 0 ? adv_x : adv_y;
-            else ui = bilinear<T>(d.phys + (long long)pc * g.np, x, yy, xx, xy, inv_dx, N);
-            val = ui - (pc == 0 ? wx : wy) - wg;
-          } else {
-            const T fi = bilinear<T>(d.phys + (long long)pc * g.np, x, yy, xx, xy, inv_dx, N);
-            val = fi - wg;
-          }
-          break;
+          const T wg = wx * x[m].x + wy * x[m].y;
+          const T fi = S[e];
+          put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wg : fi - wg);
         }
+        break;
       }
-      cplx<T>& dst = P[rr * bst + pad8(x)];
-      if (slot == 0) dst = mk<T>(val, (T)0);
-      else dst.y = val;
     }
-    if (slot == 0) {
-      pend = p;
-      slot = 1;
-    } else {
-      row_pair_forward_store<T>(P, d.pmix + (long long)pend * g.mi, d.pmix + (long long)p * g.mi, row0, B, g,
-                                d.tw);
+    if (slot == 0) pend = p;
+    slot ^= 1;
+    ++p;
+    if (slot == 0 || p == p1) {
+      cplx<T> z[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) z[m] = mk<T>(PZ[m * G + j], slot == 0 ? PZ[N + m * G + j] : (T)0);
+      group_fft<T, -1>(z, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
+      store_pair_spectrum<T>(z, buf0, buf1, w, d.pmix + (long long)pend * g.mi,
+                             slot == 0 ? d.pmix + (long long)(p - 1) * g.mi : nullptr, rowoff, j, G, grp, N, g.K,
+                             g.KXP);
       slot = 0;
     }
-    __syncthreads();
   }
-  if (slot == 1) row_pair_forward_store<T>(P, d.pmix + (long long)pend * g.mi, nullptr, row0, B, g, d.tw);
 }
 
 // ---------------------------------------------------------------------------
