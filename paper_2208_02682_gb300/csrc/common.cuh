@@ -53,6 +53,17 @@ template <typename T>
 __host__ __device__ __forceinline__ int row_stride(int N) { return N + (N >> 3); }
 template <typename T>
 __host__ __device__ __forceinline__ int col_stride(int N, int C) { return N + (N >> 3); }
+// Column tiles on group transforms (lanes interleave the C columns): each
+// column owns two exchange buffers, and successive columns are offset by a
+// number of slots (16 for FP32, 8 for FP64, per bank row) congruent to
+// slots/C, so the C lanes that share a row index use distinct slots.
+template <typename T>
+__host__ __device__ __forceinline__ int col_buf_stride(int N, int C) {
+  const int S = sizeof(T) == 4 ? 16 : 8;
+  const int st = 2 * (N + (N >> 3));
+  const int tgt = C <= S ? S / C : 1;
+  return st + (((tgt - st) % S) + S) % S;
+}
 
 // ---------------------------------------------------------------------------
 // Geometry of one grid

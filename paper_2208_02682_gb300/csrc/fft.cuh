@@ -242,9 +242,15 @@ __device__ __forceinline__ void group_pass(cplx<T>* x, const cplx<T>* in, cplx<T
   }
 }
 
-template <typename T, int SIGN, bool TWC = false>
+// BLOCK: the block's transforms step together and synchronise with
+// __syncthreads (groups whose threads interleave, e.g. column tiles).
+template <typename T, int SIGN, bool TWC = false, bool BLOCK = false>
 __device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int G, int grp, int log2N,
                           const cplx<T>* __restrict__ tw) {
+  auto sync = [&]() {
+    if (BLOCK) __syncthreads();
+    else group_sync(G, grp);
+  };
   // first pass: radix 8, stride 1, no twiddles; butterfly j takes x[0..7]
   dft8<T, SIGN>(x);
   {
@@ -252,13 +258,13 @@ __device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
 #pragma unroll
     for (int q = 0; q < 8; ++q) out[sidx<T>((j << 3) + q)] = x[q];
   }
-  group_sync(G, grp);
+  sync();
   // radix-8 passes, then the last pass (radix 8, 4 or 2) into the registers
   const int np = fft_num_passes(log2N);
   int lNs = 3;
   for (int p = 1; p < np - 1; ++p) {
     group_pass<T, SIGN, 3, false, TWC>(x, w ? buf1 : buf0, w ? buf0 : buf1, j, G, lNs, tw);
-    group_sync(G, grp);
+    sync();
     w ^= 1;
     lNs += 3;
   }

@@ -325,9 +325,9 @@ static int batch_build_t(BatchExec* b) {
     const RunDesc<T>& d = descs[r];
     const int N = h->g.N;
     const int thr[KT_COUNT] = {((1 << h->lC) * N) / 8, h->Bi * N / 8, 256, h->Bp * N / 8, ((1 << h->lC) * N) / 8, 256};
-    const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * col_stride<T>(N, 1 << h->lC) * cs,
+    const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs,
                                  (size_t)2 * h->Bi * row_stride<T>(N) * cs, 0, row_prod_smem<T>(N, h->Bp, h->L.strategy),
-                                 (size_t)(1 << h->lC) * col_stride<T>(N, 1 << h->lC) * cs, 0};
+                                 (size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs, 0};
     const KBytes kb = kernel_bytes(h, h->L);
     const double by[KT_COUNT] = {kb.col_inv, kb.row_inv, kb.phys_q, kb.row_prod, kb.col_fwd, 0.0};
     for (int k = 0; k < KT_COUNT; ++k) {

@@ -75,36 +75,91 @@ __device__ __forceinline__ const cplx<T>* stage_input(const RunDesc<T>& d, int s
 }
 
 // ---------------------------------------------------------------------------
-// a1: column inverse pass, local block = (output field, kx tile).
+// Column passes on group transforms: a block owns a tile of C = 2^lC
+// consecutive kx columns; thread t works on column c = t mod C and rows
+// n = j + m N/8 (j = t div C, m < 8), so the lanes of a warp read and write
+// C-wide contiguous runs of the kx-major fields straight from and to
+// registers.  Smem: C * col_buf_stride(N, C) complex.
+
+// a1: column inverse pass, local block = (output field, kx tile):
+// mixed = IFFT_y(op(spectral)) with op in {id, d_x, d_y, curl}, zero-padded
+// outside |ky| <= K.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_stage_col_inv(const RunDesc<T>* __restrict__ runs,
-                                                        const int* __restrict__ start, int nruns, int stage) {
+__global__ void __launch_bounds__(256) k_stage_col_inv(const RunDesc<T>* __restrict__ runs,
+                                                       const int* __restrict__ start, int nruns, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  const Geom& g = d.g;
+  const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
+  const int lC = d.lC, C = 1 << lC;
   const int lb = blockIdx.x - start[r];
-  const int ntile = d.g.KXP >> d.lC;
+  const int ntile = KXP >> lC;
   const int o = lb / ntile, tile = lb - o * ntile;
+  const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
+  const int kx = (tile << lC) + c;
   const cplx<T>* src = stage_input(d, stage);
-  const int s1 = d.L.i_src[o], s2 = d.L.i_src2[o] < 0 ? s1 : d.L.i_src2[o];
-  col_inverse_tile<T>(reinterpret_cast<cplx<T>*>(smem_raw), src + (long long)s1 * d.g.ms,
-                      src + (long long)s2 * d.g.ms, d.L.i_op[o], d.mix + (long long)o * d.g.mi, d.g, d.lC,
-                      tile << d.lC, d.tw);
+  const int op = d.L.i_op[o];
+  const cplx<T>* s1 = src + (long long)d.L.i_src[o] * g.ms;
+  const cplx<T>* s2 = src + (long long)(d.L.i_src2[o] < 0 ? d.L.i_src[o] : d.L.i_src2[o]) * g.ms;
+  cplx<T> x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = j + m * G;
+    const int ky = n <= K ? n : n - N;
+    cplx<T> v = mk<T>(0, 0);
+    if (kx <= K && (n <= K || n >= N - K)) {
+      const long long mm = (long long)(ky + K) * KXP + kx;
+      const cplx<T> a = s1[mm];
+      if (op == OP_ID) v = a;
+      else if (op == OP_DX) v = cik<T>(a, (T)kx);
+      else if (op == OP_DY) v = cik<T>(a, (T)ky);
+      else v = csub<T>(cik<T>(s2[mm], (T)kx), cik<T>(a, (T)ky));  // curl: i kx v - i ky u
+    }
+    x[m] = v;
+  }
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
+  int w = 0;
+  group_fft<T, +1, true, true>(x, b0, b0 + col_stride<T>(N, C), w, j, G, 0, g.log2N, d.tw);
+  cplx<T>* dst = d.mix + (long long)o * g.mi + kx;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) dst[(long long)(j + m * G) * KXP] = x[m];
 }
 
 // a4 (first half): column forward pass of the products, local block =
-// (product, kx tile).
+// (product, kx tile): spectral = FFT_y(mixed)/N on the rows |ky| <= K (zero
+// for kx > K).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_stage_col_fwd(const RunDesc<T>* __restrict__ runs,
-                                                        const int* __restrict__ start, int nruns) {
+__global__ void __launch_bounds__(256) k_stage_col_fwd(const RunDesc<T>* __restrict__ runs,
+                                                       const int* __restrict__ start, int nruns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  const Geom& g = d.g;
+  const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
+  const int lC = d.lC, C = 1 << lC;
   const int lb = blockIdx.x - start[r];
-  const int ntile = d.g.KXP >> d.lC;
+  const int ntile = KXP >> lC;
   const int p = lb / ntile, tile = lb - p * ntile;
-  col_forward_tile<T>(reinterpret_cast<cplx<T>*>(smem_raw), d.pmix + (long long)p * d.g.mi,
-                      d.ps + (long long)p * d.g.ms, d.g, d.lC, tile << d.lC, d.tw);
+  const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
+  const int kx = (tile << lC) + c;
+  const cplx<T>* src = d.pmix + (long long)p * g.mi + kx;
+  cplx<T> x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) x[m] = src[(long long)(j + m * G) * KXP];
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
+  int w = 0;
+  group_fft<T, -1, true, true>(x, b0, b0 + col_stride<T>(N, C), w, j, G, 0, g.log2N, d.tw);
+  const T inv = (T)1 / (T)N;
+  cplx<T>* dst = d.ps + (long long)p * g.ms + kx;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = j + m * G;
+    if (k <= K || k >= N - K) {
+      const int ky = k <= K ? k : k - N;
+      dst[(long long)(ky + K) * KXP] = kx <= K ? cscale<T>(x[m], inv) : mk<T>(0, 0);
+    }
+  }
 }
 
 // a3: Strategy-2 gather buffer (physical u, v | h, zeta), local block =
