@@ -351,7 +351,16 @@ def run_ours(args):
         ev1.record(main)
         return ev0, ev1
 
-    for _ in range(args.warmup):
+    # the library's autotuner picks the row-pass block shape for this batch
+    # (trial steps on a saved copy of the state), during the first warm-up
+    # interval
+    for h, strat in zip(hs, w.strategies):
+        lm.lmean_begin(h, lm.make_lm_params(strat, FIELDS, pos=True, eulerian=True, n_steps=n))
+    tuned = lm.sw_batch_tune(batch, 8)
+    lm.sw_batch_step(batch, n)
+    for h, o in zip(hs, outs):
+        lm.lmean_end(h, o)
+    for _ in range(max(0, args.warmup - 1)):
         interval()
     torch.cuda.synchronize()
     if dist:
@@ -362,9 +371,11 @@ def run_ours(args):
     clk.start()
     evs = []
     t_wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()
         evs.append(timed_interval())
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
@@ -458,6 +469,8 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "kernels": kernel_share, "wall_s": t_wall,
     }
+    line["config"]["row_pass_block"] = {"points": [512, 1024, 2048][tuned // 4],
+                                        "product_pairs": [1, 2, 3, "all"][tuned % 4]}
     line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
