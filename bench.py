@@ -262,6 +262,63 @@ def measure_precision(lm, torch):
             "workload": "1024^2, Ro 0.05, waves |k| 8-12, ratio 2, Strategy 1, one interval"}
 
 
+def measure_remap(lm, torch, outs, strategies, iters=20):
+    """Strategy-1 remap (lmean_remap, Eq. remap-strat1) on the bench interval's
+    own Strategy-1 outputs (256^2), compared with its Strategy-2 outputs, and
+    timed there and on a 1024^2 smooth map; algorithmic bytes per call: the
+    two position fields and the four f~^L fields read, four fbar^L fields, Xi
+    and the residual written (FP64)."""
+    res = {}
+    s1 = outs[strategies.index(1)]
+    s2 = outs[strategies.index(2)]
+    N = s1["pos_x"].shape[0]
+    r = lm.lmean_remap(s1["pos_x"], s1["pos_y"], {k: s1[k] for k in FIELDS}, iters=iters)
+    torch.cuda.synchronize()
+    x = 2 * np.pi * np.arange(N) / N
+    X = x[None, :] + 0 * x[:, None]
+    Y = x[:, None] + 0 * x[None, :]
+    agree = {}
+    for k in FIELDS:
+        a, b = r[k].cpu().numpy(), s2[k].cpu().numpy()
+        agree[k] = float(np.linalg.norm(a - b) / np.linalg.norm(b - b.mean()))
+    xi1 = np.concatenate([(r["xi_x"].cpu().numpy() - X).ravel(), (r["xi_y"].cpu().numpy() - Y).ravel()])
+    xi2 = np.concatenate([(s2["pos_x"].cpu().numpy() - X).ravel(), (s2["pos_y"].cpu().numpy() - Y).ravel()])
+    agree["xi"] = float(np.linalg.norm(xi1 - xi2) / np.linalg.norm(xi2))
+    res["strategy1_remapped_vs_strategy2_rel_l2"] = agree
+    res["max_resid"] = float(r["resid"].max().item())
+
+    def timed(pos_x, pos_y, fields, reps=20):
+        for _ in range(3):
+            lm.lmean_remap(pos_x, pos_y, fields, iters=iters)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            lm.lmean_remap(pos_x, pos_y, fields, iters=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    times = {N: timed(s1["pos_x"], s1["pos_y"], {k: s1[k] for k in FIELDS})}
+    M = 1024
+    rng = np.random.Generator(np.random.PCG64(1024))
+    xm = 2 * np.pi * np.arange(M) / M
+    XM, YM = np.meshgrid(xm, xm)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    px = dev(XM - 0.2 * np.sin(YM + 0.3) - 0.05 * si.random_smooth_field(M, 3, rng))
+    py = dev(YM - 0.2 * np.sin(XM - 0.7) - 0.05 * si.random_smooth_field(M, 3, rng))
+    fm = {k: dev(si.random_smooth_field(M, 8, rng)) for k in FIELDS}
+    times[M] = timed(px, py, fm)
+    res["ms"] = {str(k): v for k, v in times.items()}
+    res["grid_points_per_s"] = {str(k): k * k / (v * 1e-3) for k, v in times.items()}
+    nbytes = lambda n: (2 + len(FIELDS) + len(FIELDS) + 3) * n * n * 8
+    res["algorithmic_GBps"] = {str(k): nbytes(k) / (v * 1e-3) / 1e9 for k, v in times.items()}
+    res["iters"] = iters
+    res["workload"] = ("bench interval's Strategy-1 outputs (256^2: zeta, h, u, v, positions) and a 1024^2 "
+                       "smooth random map with four fields; FP64")
+    return res
+
+
 def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
     """Poisson stream of Lagrangian-mean requests through sw_server."""
     import time as _t
@@ -447,6 +504,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras:
+        extras["remap"] = measure_remap(lm, torch, outs, list(w.strategies))
         extras["batched"] = measure_batched(lm, torch)
         extras["precision_form"] = measure_precision(lm, torch)
         extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)

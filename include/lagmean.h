@@ -347,12 +347,48 @@ int64_t sw_state_bytes(const sw_params* p);
 #define SW_PROJECT_STATIC_BYTES (3u << 20)
 int sw_project_static(const double* in, double* out, int N, void* stream);
 
+/* ---- Strategy-1 remap to the mean-position grid ---------------------------
+ * Sec. 3.1, Eq. (remap-strat1): f~^L(x, tau) = fbar^L(Xi^{-1}(x, tau+T), tau).
+ * Strategy 1 (lmean_end with strategy 1) yields f~^L and the mean positions
+ * Xi^{-1}(x, tau+T) on the grid x, i.e. fbar^L at scattered points.  This
+ * call returns fbar^L on the grid y of mean positions by evaluating
+ * f~^L at Xi(y), Xi = (Xi^{-1})^{-1} the lift map of Eq. (Xi-def): with the
+ * periodic displacement d = x - Xi^{-1}(x), Xi(y) = y + xi(y) where xi is the
+ * fixed point of xi = d(y + xi), iterated `iters` times from xi = 0, and
+ * off-grid values of d and f~^L are bilinear interpolants (cell index
+ * i + floor(xi/dx), periodic; the rule of the Strategy-2 solver, Sec.
+ * 4.2.1).  The paper does not fix the interpolation; the fixed point
+ * converges while Xi^{-1} stays invertible (|grad d| < 1), and `resid`
+ * reports the last update so callers can see where it does not (the mean
+ * positions cluster, Sec. 5).  FP64; every arithmetic step is rounded
+ * separately (no fused multiply-add), so results are reproducible bit for bit.
+ *   N:            power of two in [16, 4096].
+ *   pos_x, pos_y: device, N*N doubles each (row-major, y slow): Xi^{-1} at the
+ *                 grid points, as lmean_end reports it (unwrapped).
+ *   nfields:      0..LM_REMAP_MAX_FIELDS.
+ *   ftilde:       HOST array of nfields device pointers, N*N doubles each
+ *                 (f~^L on the grid x).
+ *   fbar:         HOST array of nfields device pointers, N*N doubles each,
+ *                 written with fbar^L on the grid y.  Must not alias any
+ *                 input (the gathers read neighbouring points).
+ *   iters:        fixed-point iterations, 1..10000 (20 is ample for
+ *                 |grad d| < 0.25).
+ *   xi_x, xi_y:   device N*N doubles or NULL: Xi(y) = y + xi (unwrapped).
+ *   resid:        device N*N doubles or NULL: max(|dxi_x|, |dxi_y|) of the last
+ *                 iteration at each point.
+ *   stream:       cudaStream_t (NULL: legacy default stream); asynchronous.
+ * The caller owns every buffer.  Errors: SW_EINVAL (message via
+ * sw_last_error(NULL)), SW_ECUDA. */
+#define LM_REMAP_MAX_FIELDS 16
+int lmean_remap(int N, const double* pos_x, const double* pos_y, int nfields, const double* const* ftilde,
+                double* const* fbar, int iters, double* xi_x, double* xi_y, double* resid, void* stream);
+
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);
 
 /* Message for the last failing call on h ("" if none); valid until the next
- * call on h.  With h == NULL, the message of the last failing sw_create or
- * sw_project_static on the calling thread. */
+ * call on h.  With h == NULL, the message of the last failing sw_create,
+ * sw_project_static or lmean_remap on the calling thread. */
 const char* sw_last_error(sw_handle* h);
 
 /* Library version string. */

@@ -29,7 +29,7 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "sw_launch_count", "sw_project_static", "sw_batch_create", "sw_batch_step",
            "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
            "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
-           "sw_server_clock", "sw_server_destroy", "sw_state_bytes")
+           "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH):
         "sw_kernel_times": (C.c_int, [H, C.c_int64, _DP, C.POINTER(C.c_int64), _DP]),
         "sw_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "sw_project_static": (C.c_int, [_DP, _DP, C.c_int, C.c_void_p]),
+        "lmean_remap": (C.c_int, [C.c_int, _DP, _DP, C.c_int, C.POINTER(_DP), C.POINTER(_DP), C.c_int, _DP, _DP,
+                                  _DP, C.c_void_p]),
         "sw_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(H)]),
         "sw_batch_step": (C.c_int, [H, C.c_int64]),
         "sw_batch_tune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
@@ -431,6 +433,43 @@ def sw_project_static(inp, out, N, stream=None):
         raise ValueError("sw_project_static takes device tensors")
     lib = load()
     rc = lib.sw_project_static(pi, po, int(N), C.c_void_p(stream or 0))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return out
+
+
+def lmean_remap(pos_x, pos_y, ftilde, iters=20, xi=True, resid=True, stream=None):
+    """Strategy-1 means onto the mean-position grid, Eq. (remap-strat1) (see
+    include/lagmean.h).  pos_x, pos_y: Xi^{-1} at the grid points; ftilde: dict
+    name -> f~^L; all contiguous float64 CUDA tensors of shape (N, N).
+    Returns a dict with the fbar^L fields under the same names, plus
+    "xi_x"/"xi_y" (Xi at the grid points) and "resid" when requested."""
+    import torch
+
+    N = int(pos_x.shape[-1])
+    names = list(ftilde)
+    out = {k: torch.empty_like(pos_x) for k in names}
+    if xi:
+        out["xi_x"] = torch.empty_like(pos_x)
+        out["xi_y"] = torch.empty_like(pos_x)
+    if resid:
+        out["resid"] = torch.empty_like(pos_x)
+    px, dx_ = _ptr(pos_x)
+    py, dy_ = _ptr(pos_y)
+    if not (dx_ and dy_):
+        raise ValueError("lmean_remap takes device tensors")
+    fin = (_DP * max(1, len(names)))()
+    fout = (_DP * max(1, len(names)))()
+    for i, k in enumerate(names):
+        p, d = _ptr(ftilde[k])
+        if not d or tuple(ftilde[k].shape) != (N, N):
+            raise ValueError("ftilde fields must be (N, N) float64 CUDA tensors")
+        fin[i] = p
+        fout[i] = _ptr(out[k])[0]
+    opt = [_ptr(out[k])[0] if k in out else None for k in ("xi_x", "xi_y", "resid")]
+    lib = load()
+    rc = lib.lmean_remap(N, px, py, len(names), fin, fout, int(iters), opt[0], opt[1], opt[2],
+                         C.c_void_p(stream or 0))
     if rc != SW_OK:
         raise SWError(rc, lib.sw_last_error(None).decode())
     return out

@@ -88,3 +88,35 @@ def test_null_handle_is_rejected(lm):
     assert lib.lmean_begin(None, None) == lm.api.SW_EINVAL
     assert lib.sw_sync(None) == lm.api.SW_EINVAL
     lib.sw_destroy(None)  # no-op
+
+
+@pytest.mark.parametrize("case", ["N_not_pow2", "N_too_big", "iters_zero", "too_many_fields", "alias_in",
+                                  "alias_out", "null_pos"])
+def test_remap_arguments_rejected_before_device_use(lm, case):
+    # every case is invalid, so the call returns before touching the (fake)
+    # device addresses or launching anything
+    lib = lm.api.load()
+    DP = lm.api._DP
+    fake = [C.cast(C.c_void_p(0x10000 * (k + 1)), DP) for k in range(8)]
+    N, iters, nf = 64, 20, 1
+    pos_x, pos_y = fake[0], fake[1]
+    fin = (DP * 1)(fake[2])
+    fout = (DP * 1)(fake[3])
+    xi_x = fake[4]
+    if case == "N_not_pow2":
+        N = 48
+    elif case == "N_too_big":
+        N = 8192
+    elif case == "iters_zero":
+        iters = 0
+    elif case == "too_many_fields":
+        nf = 17
+    elif case == "alias_in":
+        fout = (DP * 1)(fake[2])
+    elif case == "alias_out":
+        xi_x = fake[3]
+    elif case == "null_pos":
+        pos_y = None
+    rc = lib.lmean_remap(N, pos_x, pos_y, nf, fin, fout, iters, xi_x, None, None, None)
+    assert rc == lm.api.SW_EINVAL
+    assert "lmean_remap" in lm.sw_last_error(None)
