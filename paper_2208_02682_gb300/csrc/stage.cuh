@@ -415,6 +415,99 @@ __device__ __forceinline__ double kahan_add_rn(double sum, double add, double& c
   return t;
 }
 
+// Right-hand side and RK4 update of evolved field f at mode m = kyi*KXP + kx
+// (kx <= K); prod(p) returns the spectral product p at this mode.
+template <typename T, typename PF>
+__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, double sd, int f, long long m, int kx,
+                                            int kyi, PF prod) {
+  const Geom& g = d.g;
+  const Layout& L = d.L;
+  const T kxf = (T)kx, kyf = (T)(kyi - g.K);
+  const T dt = (T)d.c.dt;
+  const cplx<T>* yin = stage_input(d, stage);
+  const int role = L.frole[f], slot = L.fslot[f];
+  cplx<T> rhs;
+  if (role <= R_H) {
+    // shallow-water right-hand side, Eq. (sw_eqs_dimless)
+    if (L.model == 0) {
+      if (role == R_H) {
+        rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(prod(L.p_hu), kxf), cik<T>(prod(L.p_hv), kyf)));
+      } else {
+        const cplx<T> hh = yin[L.f_h * g.ms + m];
+        const cplx<T> Bq = cadd<T>(cscale<T>(hh, (T)d.c.c2), prod(L.p_ke));
+        if (role == R_U)
+          rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], (T)d.c.f0), prod(L.p_zv)), cik<T>(Bq, kxf));
+        else
+          rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -(T)d.c.f0), prod(L.p_zu)), cik<T>(Bq, kyf));
+      }
+    } else {
+      const T kc = kxf * (T)d.c.adv_x + kyf * (T)d.c.adv_y;
+      rhs = cik<T>(yin[f * g.ms + m], -kc);
+    }
+  } else if (role == R_P) {
+    const cplx<T> pp = prod(L.p_p[slot]);
+    if (L.strategy == 1) {
+      // d_t D = s u - u.grad D
+      cplx<T> ua;
+      if (L.model == 1) {
+        const bool k0 = (kx == 0 && kyi == g.K);
+        ua = mk<T>(k0 ? (T)(slot == 0 ? d.c.adv_x : d.c.adv_y) : (T)0, 0);
+      } else {
+        ua = yin[(slot == 0 ? L.f_u : L.f_v) * g.ms + m];
+      }
+      rhs = csub<T>(cscale<T>(ua, (T)sd), pp);
+    } else {
+      rhs = pp;  // xi: the product holds u(x+xi) - w - w.grad xi
+    }
+  } else {
+    // f_hat of the averaged scalar at this stage
+    const int sc = L.lmf[slot];
+    cplx<T> fh;
+    if (sc == LMF_ZETA) fh = csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
+    else if (sc == LMF_H) fh = yin[L.f_h * g.ms + m];
+    else if (sc == LMF_U) fh = yin[L.f_u * g.ms + m];
+    else if (sc == LMF_V) fh = yin[L.f_v * g.ms + m];
+    else fh = prod(L.p_q);
+    if (role == R_E) {
+      rhs = fh;  // Eq. (ave)
+    } else {
+      const cplx<T> pg = prod(L.p_g[slot]);
+      // S1: f - u.grad g (Eq. gtilde-evol); S2: f(x+xi) - w.grad g
+      rhs = L.strategy == 1 ? csub<T>(fh, pg) : pg;
+    }
+  }
+  const int cls = L.fclass[f];
+  const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
+  const long long o = f * g.ms + m;
+  const cplx<T> yn = d.y[o];
+  cplx<T>* yout = stage == 1 ? d.ysb : d.ysa;
+  if (stage == 0) {
+    d.acc[o] = cscale<T>(rhs, E * E);
+    yout[o] = cscale<T>(cadd<T>(yn, cscale<T>(rhs, (T)0.5 * dt)), E);
+  } else if (stage == 1) {
+    d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
+    yout[o] = cadd<T>(cscale<T>(yn, E), cscale<T>(rhs, (T)0.5 * dt));
+  } else if (stage == 2) {
+    d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
+    yout[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(rhs, dt * E));
+  } else {
+    const cplx<T> inc = cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)6);
+    const T E2 = E * E;
+    if (d.comp && L.fkahan[f]) {
+      cplx<T> cc = d.comp[o];
+      cc.x *= E2;
+      cc.y *= E2;
+      cplx<T> out;
+      out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
+      out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
+      d.y[o] = out;
+      d.comp[o] = cc;
+    } else {
+      d.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restrict__ runs,
                                                       const int* __restrict__ start, int nruns, int stage) {
@@ -430,91 +523,7 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
   if (m < g.ms) {
     const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
     if (kx <= g.K) {
-      const T kxf = (T)kx, kyf = (T)(kyi - g.K);
-      const T dt = (T)d.c.dt;
-      const cplx<T>* yin = stage_input(d, stage);
-      const cplx<T>* ps = d.ps;
-      const int role = L.frole[f], slot = L.fslot[f];
-      cplx<T> rhs;
-      if (role <= R_H) {
-        // shallow-water right-hand side, Eq. (sw_eqs_dimless)
-        if (L.model == 0) {
-          if (role == R_H) {
-            rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(ps[L.p_hu * g.ms + m], kxf), cik<T>(ps[L.p_hv * g.ms + m], kyf)));
-          } else {
-            const cplx<T> hh = yin[L.f_h * g.ms + m];
-            const cplx<T> Bq = cadd<T>(cscale<T>(hh, (T)d.c.c2), ps[L.p_ke * g.ms + m]);
-            if (role == R_U)
-              rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], (T)d.c.f0), ps[L.p_zv * g.ms + m]), cik<T>(Bq, kxf));
-            else
-              rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -(T)d.c.f0), ps[L.p_zu * g.ms + m]), cik<T>(Bq, kyf));
-          }
-        } else {
-          const T kc = kxf * (T)d.c.adv_x + kyf * (T)d.c.adv_y;
-          rhs = cik<T>(yin[f * g.ms + m], -kc);
-        }
-      } else if (role == R_P) {
-        const cplx<T> pp = ps[L.p_p[slot] * g.ms + m];
-        if (L.strategy == 1) {
-          // d_t D = s u - u.grad D
-          cplx<T> ua;
-          if (L.model == 1) {
-            const bool k0 = (kx == 0 && kyi == g.K);
-            ua = mk<T>(k0 ? (T)(slot == 0 ? d.c.adv_x : d.c.adv_y) : (T)0, 0);
-          } else {
-            ua = yin[(slot == 0 ? L.f_u : L.f_v) * g.ms + m];
-          }
-          rhs = csub<T>(cscale<T>(ua, (T)sd), pp);
-        } else {
-          rhs = pp;  // xi: the product holds u(x+xi) - w - w.grad xi
-        }
-      } else {
-        // f_hat of the averaged scalar at this stage
-        const int sc = L.lmf[slot];
-        cplx<T> fh;
-        if (sc == LMF_ZETA) fh = csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
-        else if (sc == LMF_H) fh = yin[L.f_h * g.ms + m];
-        else if (sc == LMF_U) fh = yin[L.f_u * g.ms + m];
-        else if (sc == LMF_V) fh = yin[L.f_v * g.ms + m];
-        else fh = ps[L.p_q * g.ms + m];
-        if (role == R_E) {
-          rhs = fh;  // Eq. (ave)
-        } else {
-          const cplx<T> pg = ps[L.p_g[slot] * g.ms + m];
-          // S1: f - u.grad g (Eq. gtilde-evol); S2: f(x+xi) - w.grad g
-          rhs = L.strategy == 1 ? csub<T>(fh, pg) : pg;
-        }
-      }
-      const int cls = L.fclass[f];
-      const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
-      const long long o = f * g.ms + m;
-      const cplx<T> yn = d.y[o];
-      cplx<T>* yout = stage == 1 ? d.ysb : d.ysa;
-      if (stage == 0) {
-        d.acc[o] = cscale<T>(rhs, E * E);
-        yout[o] = cscale<T>(cadd<T>(yn, cscale<T>(rhs, (T)0.5 * dt)), E);
-      } else if (stage == 1) {
-        d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
-        yout[o] = cadd<T>(cscale<T>(yn, E), cscale<T>(rhs, (T)0.5 * dt));
-      } else if (stage == 2) {
-        d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
-        yout[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(rhs, dt * E));
-      } else {
-        const cplx<T> inc = cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)6);
-        const T E2 = E * E;
-        if (d.comp && L.fkahan[f]) {
-          cplx<T> cc = d.comp[o];
-          cc.x *= E2;
-          cc.y *= E2;
-          cplx<T> out;
-          out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
-          out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
-          d.y[o] = out;
-          d.comp[o] = cc;
-        } else {
-          d.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
-        }
-      }
+      update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
     }
   }
   if (stage == 3) {
