@@ -527,7 +527,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "kernels": kernel_share, "wall_s": t_wall,
     }
-    line["config"]["row_pass_block"] = {"points": [512, 1024, 2048][tuned // 4],
+    line["config"]["row_pass_block"] = {"points": [256, 512, 1024, 2048][tuned // 4],
                                         "product_pairs": [1, 2, 3, "all"][tuned % 4]}
     line.update(extras)
     print(json.dumps(line), flush=True)

@@ -226,10 +226,11 @@ int sw_batch_create(sw_handle* const* handles, int n, sw_batch** out);
  * in a member's open interval (nothing is stepped then).  Asynchronous. */
 int sw_batch_step(sw_batch* b, int64_t nsteps);
 
-/* Autotuner: times the row-pass launch shapes (points per block 512, 1024 or
- * 2048; product pairs per block 1, 2, 3 or all) on trial_steps >= 1 replayed
- * steps each, keeps the fastest for all members and returns its index in
- * *choice (may be NULL).  The members' states are saved before the trials and
+/* Autotuner: times the row-pass launch shapes (points per block 256, 512,
+ * 1024 or 2048, as long as every member fits; product pairs per block 1, 2, 3
+ * or all; choice = 4 * points index + pairs index) on trial_steps >= 1
+ * replayed steps each, keeps the fastest for all members and returns its
+ * index in *choice (may be NULL).  The members' states are saved before the trials and
  * restored after them (temporary device copies).  Synchronises. */
 int sw_batch_tune(sw_batch* b, int trial_steps, int* choice);
 

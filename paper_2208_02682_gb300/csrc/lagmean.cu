@@ -295,6 +295,7 @@ static void fill_desc(sw_handle* h, RunDesc<T>& d) {
   d.lC = h->lC;
   d.Bp = h->Bp;
   d.ppb = h->ppb;
+  d.Wp = 1;
   d.Bi = h->Bi;
   const Layout& L = h->L;
   const int ntile = g.KXP >> h->lC;
@@ -319,14 +320,28 @@ static int batch_build_t(BatchExec* b) {
   }
   b->start.assign((size_t)KT_COUNT * (n + 1), 0);
   const size_t cs = sizeof(cplx<T>);
+  // row-pass groups per row: the largest number every member allows (the
+  // batch's row-pass blocks all have Bp * Wp * N/8 threads)
+  int W = 1 << 20;
+  for (int r = 0; r < n; ++r) {
+    const sw_handle* h = b->members[r];
+    const int npairs = (h->L.np + 1) / 2;
+    const int npb = h->ppb < npairs ? h->ppb : npairs;
+    const int w = row_prod_groups<T>(h->g.N, h->Bp, npb, h->L.strategy);
+    W = w < W ? w : W;
+  }
+  if (n == 0) W = 1;
   for (int r = 0; r < n; ++r) {
     sw_handle* h = b->members[r];
     fill_desc<T>(h, descs[r]);
+    descs[r].Wp = W;
     const RunDesc<T>& d = descs[r];
     const int N = h->g.N;
-    const int thr[KT_COUNT] = {((1 << h->lC) * N) / 8, h->Bi * N / 8, 256, h->Bp * N / 8, ((1 << h->lC) * N) / 8, 256};
+    const int thr[KT_COUNT] = {((1 << h->lC) * N) / 8, h->Bi * N / 8, 256, h->Bp * W * N / 8,
+                               ((1 << h->lC) * N) / 8, 256};
     const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs,
-                                 (size_t)2 * h->Bi * row_stride<T>(N) * cs, 0, row_prod_smem<T>(N, h->Bp, h->L.strategy),
+                                 (size_t)2 * h->Bi * row_stride<T>(N) * cs, 0,
+                                 row_prod_smem<T>(N, h->Bp, W, h->L.strategy),
                                  (size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs, 0};
     const KBytes kb = kernel_bytes(h, h->L);
     const double by[KT_COUNT] = {kb.col_inv, kb.row_inv, kb.phys_q, kb.row_prod, kb.col_fwd, 0.0};
@@ -732,7 +747,8 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   h->diag_blocks = DIAG_BLOCKS;
   h->Bp = row_block_rows(g.N);
   h->Bi = row_block_rows(g.N);
-  h->ppb = g.N <= 512 ? 1 : MAXP;
+  // all product pairs per block: the row's groups share them out
+  h->ppb = MAXP;
   const ArenaPlan A = plan_arena(g, h->tsz);
   const size_t o_y = A.o[0], o_ys = A.o[1], o_ys2 = A.o[2], o_acc = A.o[3], o_comp = A.o[4], o_ps = A.o[5];
   const size_t o_mix = A.o[6], o_pmix = A.o[7], o_phys = A.o[8], o_ef = A.o[9], o_tw = A.o[10];
@@ -1214,7 +1230,7 @@ extern "C" int sw_batch_tune(sw_batch* b, int trial_steps, int* choice) {
   BatchExec* ex = b->ex;
   int maxN = 0;
   for (sw_handle* h : ex->members) maxN = h->g.N > maxN ? h->g.N : maxN;
-  const int pts[3] = {512, 1024, 2048};
+  const int pts[4] = {256, 512, 1024, 2048};
   const int ppbs[4] = {1, 2, 3, MAXP};
   std::vector<Saved> saved(ex->members.size());
   cudaError_t e = cudaSuccess;
@@ -1241,9 +1257,9 @@ extern "C" int sw_batch_tune(sw_batch* b, int trial_steps, int* choice) {
     rc = bfail(b, SW_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
   int best = -1;
   float best_ms = 0.f;
-  for (int ci = 0; rc == SW_OK && ci < 12; ++ci) {
+  for (int ci = 0; rc == SW_OK && ci < 16; ++ci) {
     const int P = pts[ci / 4], ppb = ppbs[ci % 4];
-    if (P < maxN && ci / 4 > 0) continue;  // same shape as a smaller P for the largest member
+    if (P < maxN) continue;  // every member needs rows x N = P (equal block shapes)
     for (sw_handle* h : ex->members) {
       h->Bp = row_block_rows(h->g.N, P);
       h->ppb = ppb;
@@ -1269,7 +1285,11 @@ extern "C" int sw_batch_tune(sw_batch* b, int trial_steps, int* choice) {
     }
   }
   if (rc == SW_OK && e != cudaSuccess) rc = bfail(b, SW_ECUDA, std::string("tuning trial: ") + cudaGetErrorString(e));
-  if (best < 0) best = 0;
+  if (best < 0) {  // no trial ran: the default shape (512 points or one row, all pairs)
+    int pi = 1;
+    while (pi < 3 && pts[pi] < maxN) ++pi;
+    best = 4 * pi + 3;
+  }
   for (sw_handle* h : ex->members) {
     h->Bp = row_block_rows(h->g.N, pts[best / 4]);
     h->ppb = ppbs[best % 4];

@@ -9,14 +9,32 @@ namespace lm {
 // threads (one 8-element Stockham butterfly set per thread and pass).
 // `points` = B*N; 512 keeps small grids spread over many SMs.
 inline int row_block_rows(int N, int points = 512) {
+  // points = rows x N per block (the block runs points/8 threads per group)
   int B = points / N;
   if (B > N) B = N;
   if (B < 1) B = 1;
   return B;
 }
 
-template <typename T> size_t row_prod_smem(int N, int B, int strategy) {
-  return (size_t)B * (2 * row_stride<T>(N) * sizeof(cplx<T>) + (size_t)(strategy == 2 ? 9 : 6) * N * sizeof(T));
+// Row pass: B rows per block, W groups of N/8 threads per row (see
+// k_stage_row_prod); the block may hold up to row_prod_max_threads threads.
+template <typename T> size_t row_prod_smem(int N, int B, int W, int strategy) {
+  const size_t nur = strategy == 2 ? 6 : 4, nug = strategy == 2 ? 3 : 2;
+  return (size_t)B * nur * N * sizeof(T) +
+         (size_t)B * W * (2 * row_stride<T>(N) * sizeof(cplx<T>) + nug * N * sizeof(T));
+}
+
+// Largest W for B rows and npb product pairs per block: W > 1 needs whole
+// warps per group (N >= 256), a thread count within the block limit, at most
+// 15 named barriers (groups of N >= 512) and 200 KB of shared memory.
+template <typename T> int row_prod_groups(int N, int B, int npb, int strategy) {
+  const int G = N / 8;
+  if (G < 32) return 1;
+  int W = npb < 1 ? 1 : npb;
+  while (W > 1 && (B * W * G > row_prod_max_threads<T>() || (G >= 64 && B * W > 15) ||
+                   row_prod_smem<T>(N, B, W, strategy) > (size_t)200 * 1024))
+    --W;
+  return W;
 }
 
 template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStream_t s);

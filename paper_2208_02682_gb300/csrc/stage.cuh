@@ -36,6 +36,7 @@ struct RunDesc {
   unsigned* ticket;
   int lC;         // column tile: C = 2^lC columns
   int Bp, ppb;    // row_prod: rows per block, product pairs per block
+  int Wp;         // row_prod: groups of N/8 threads per row
   int Bi;         // row_inv: rows per block
   int nb[KT_COUNT];
 };
@@ -208,37 +209,51 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 }
 
 // ---------------------------------------------------------------------------
-// a2: row pass with products.  Local block = (pair group, row block): Bp rows,
-// one per group of G = N/8 threads, and product pairs [grp*ppb,
-// (grp+1)*ppb).  Every transform stays in the registers of its group
-// (group_fft): a row's physical values live at the thread's own positions
-// x = j + m G, where the products are formed and the forward transform of
-// each product pair starts.  Smem per group: two exchange buffers of
-// row_stride(N) complex, then U (u, v, h, zeta), for Strategy 2 XI (xi_x,
-// xi_y) and S (gathered values), and PZ (the two products of a pair), N
-// reals each, read back only by the thread that wrote them.
+// a2: row pass with products.  Local block = (pair group, row block): Bp rows
+// and product pairs [pg*ppb, (pg+1)*ppb), with Wp groups of G = N/8 threads
+// per row.  Every transform stays in the registers of its group (group_fft):
+// a row's physical values live at the thread's own positions x = j + m G,
+// where the products are formed and the forward transform of each product
+// pair starts.  First the row's base fields (u, v | h, zeta; Strategy 2: xi,
+// with u, v, h, zeta read from the gather buffer) are transformed, the steps
+// shared out over the row's groups, into the row's U; then the groups take
+// the block's product pairs in turn.  Wp > 1 only when a group is a whole
+// number of warps (N >= 256), so groups that do different numbers of
+// transforms never share a warp barrier.
+// Smem: per row U (u, v, h, zeta and, Strategy 2, xi_x, xi_y: N reals each);
+// per group two exchange buffers of row_stride(N) complex, PZ (the two
+// products of a pair) and, Strategy 2, S (gathered values), N reals each.
+
+// Threads per row-pass block at most (two blocks per SM: up to 85 registers
+// in FP32, 128 in FP64).
+template <typename T> constexpr int row_prod_max_threads() { return sizeof(T) == 4 ? 384 : 256; }
+
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
-                                                        const int* __restrict__ start, int nruns, int stage) {
+__global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
+                                                                                const int* __restrict__ start,
+                                                                                int nruns, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   const Geom& g = d.g;
   const Layout& L = d.L;
-  const int N = g.N, B = d.Bp, G = N >> 3;
+  const int N = g.N, B = d.Bp, W = d.Wp, G = N >> 3;
   const int lb = blockIdx.x - start[r];
   const int nrb = N / B;
   const int pg = lb / nrb, rb = lb - pg * nrb;
-  const int grp = threadIdx.x / G, j = threadIdx.x - grp * G;
-  const int y = rb * B + grp;
+  const int gi = threadIdx.x / G, j = threadIdx.x - gi * G;
+  const int row = gi / W, wg = gi - row * W;
+  const int y = rb * B + row;
   const int rs = row_stride<T>(N);
-  const int nu = L.strategy == 2 ? 7 : 4;  // + 2 for PZ
-  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
-  cplx<T>* buf1 = buf0 + rs;
-  T* U = reinterpret_cast<T*>(reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)B * 2 * rs) + (size_t)grp * (nu + 2) * N;
+  const bool s2 = L.strategy == 2;
+  const int nur = s2 ? 6 : 4, nug = s2 ? 3 : 2;
+  T* U = reinterpret_cast<T*>(smem_raw) + (size_t)row * nur * N;
   T* XI = U + 4 * N;
-  T* S = U + 6 * N;
-  T* PZ = U + nu * N;
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(reinterpret_cast<T*>(smem_raw) + (size_t)B * nur * N) +
+                  (size_t)gi * (2 * rs + (nug * N) / 2);
+  cplx<T>* buf1 = buf0 + rs;
+  T* PZ = reinterpret_cast<T*>(buf1 + rs);
+  T* S = PZ + 2 * N;
   const int np = L.np;
   const int p0 = pg * d.ppb * 2;
   const int p1 = min(np, p0 + d.ppb * 2);
@@ -252,6 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_stage_row_prod(
   const cplx<T>* mix = d.mix;
   const long long rowoff = (long long)y * g.KXP;
   int w = 0;
+  cplx<T> x[8];
 
   // which physical base fields this block's products read
   bool need_uv = false, need_hz = false;
@@ -261,16 +277,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_stage_row_prod(
     if (k == PK_ZV || k == PK_ZU || k == PK_KE || k == PK_HU || k == PK_HV) need_uv = true;
     if ((k == PK_ADV || k == PK_XI || k == PK_GBAR) && !kin) need_uv = true;
   }
-  // Inverse steps before the products: base pairs into U (and XI).  Strategy
-  // 2 reads u, v, h, zeta from the gather buffer and transforms xi only.
+  // base fields of the row into U (and XI)
   int base_a[2], base_b[2], base_o[2];
   int nbase = 0;
-  if (L.strategy == 2) {
+  if (s2) {
+    if (wg == 0) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const long long off = (long long)y * N + j + m * G;
+      for (int m = 0; m < 8; ++m) {
+        const long long off = (long long)y * N + j + m * G;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) U[f * N + m * G + j] = d.phys[f * g.np + off];
+        for (int f = 0; f < 4; ++f) U[f * N + m * G + j] = d.phys[f * g.np + off];
+      }
     }
     base_a[0] = L.i_xi[0], base_b[0] = L.i_xi[1], base_o[0] = 4;
     nbase = 1;
@@ -278,118 +295,112 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_stage_row_prod(
     if (need_uv) base_a[nbase] = L.i_u, base_b[nbase] = L.i_v, base_o[nbase] = 0, ++nbase;
     if (need_hz) base_a[nbase] = L.i_h, base_b[nbase] = L.i_z, base_o[nbase] = 2, ++nbase;
   }
+  for (int t = wg; t < nbase; t += W) {
+    load_pair_spectrum<T>(x, mix + (long long)base_a[t] * g.mi, mix + (long long)base_b[t] * g.mi, rowoff, j, G, N,
+                          g.K);
+    group_fft<T, +1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    T* dst = U + base_o[t] * N;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      dst[m * G + j] = x[m].x;
+      dst[N + m * G + j] = x[m].y;
+    }
+  }
+  __syncthreads();
 
-  // One loop over the inverse steps and the products, so that each direction
-  // of the group transform is instantiated once.
-  cplx<T> x[8];
-  int slot = 0, pend = -1;
-  int t = 0, p = p0;
-  while (t < nbase || p < p1) {
-    const bool is_base = t < nbase;
-    const int kind = is_base ? -1 : L.pk[p];
-    const bool need_inv = is_base || kind == PK_ADV || kind == PK_XI || kind == PK_GBAR;
-    if (need_inv) {
-      const int ia = is_base ? base_a[t] : L.pa[p], ib = is_base ? base_b[t] : L.pb[p];
-      load_pair_spectrum<T>(x, mix + (long long)ia * g.mi, mix + (long long)ib * g.mi, rowoff, j, G, N, g.K);
-      group_fft<T, +1>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
-    }
-    if (is_base) {
-      T* dst = U + base_o[t] * N;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        dst[m * G + j] = x[m].x;
-        dst[N + m * G + j] = x[m].y;
+  // product pairs, shared out over the row's groups
+  const int npair = (p1 - p0 + 1) >> 1;
+  for (int q = wg; q < npair; q += W) {
+    const int pa = p0 + 2 * q;
+    const int npq = min(2, p1 - pa);
+    for (int slot = 0; slot < npq; ++slot) {
+      const int p = pa + slot;
+      const int kind = L.pk[p];
+      if (kind == PK_ADV || kind == PK_XI || kind == PK_GBAR) {
+        load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
+                              g.K);
+        group_fft<T, +1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
       }
-      ++t;
-      continue;
-    }
-    const int pc = L.pc[p];
-    // value of this product at position m: slot `slot` of the pair in PZ
-    T* const pz = PZ + slot * N;
-    auto put = [&](int m, T v) { pz[m * G + j] = v; };
-    switch (kind) {
-      case PK_ZV:
+      const int pc = L.pc[p];
+      T* const pz = PZ + slot * N;
+      auto put = [&](int m, T v) { pz[m * G + j] = v; };
+      switch (kind) {
+        case PK_ZV:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[N + m * G + j]);
-        break;
-      case PK_ZU:
+          for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[N + m * G + j]);
+          break;
+        case PK_ZU:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[m * G + j]);
-        break;
-      case PK_KE:
+          for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[m * G + j]);
+          break;
+        case PK_KE:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const T u = U[m * G + j], v = U[N + m * G + j];
-          put(m, (T)0.5 * (u * u + v * v));
-        }
-        break;
-      // depth h = 1 + eta; the state and the row buffers hold eta
-      case PK_HU:
+          for (int m = 0; m < 8; ++m) {
+            const T u = U[m * G + j], v = U[N + m * G + j];
+            put(m, (T)0.5 * (u * u + v * v));
+          }
+          break;
+        // depth h = 1 + eta; the state and the row buffers hold eta
+        case PK_HU:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const T u = U[m * G + j];
-          put(m, u + U[2 * N + m * G + j] * u);
-        }
-        break;
-      case PK_HV:
+          for (int m = 0; m < 8; ++m) {
+            const T u = U[m * G + j];
+            put(m, u + U[2 * N + m * G + j] * u);
+          }
+          break;
+        case PK_HV:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const T v = U[N + m * G + j];
-          put(m, v + U[2 * N + m * G + j] * v);
-        }
-        break;
-      case PK_Q:
+          for (int m = 0; m < 8; ++m) {
+            const T v = U[N + m * G + j];
+            put(m, v + U[2 * N + m * G + j] * v);
+          }
+          break;
+        case PK_Q:
 #pragma unroll
-        for (int m = 0; m < 8; ++m) put(m, (f0 + U[3 * N + m * G + j]) / ((T)1 + U[2 * N + m * G + j]));
-        break;
-      case PK_ADV:
-        // u.grad G (Eq. gtilde-evol) or u.grad D
+          for (int m = 0; m < 8; ++m) put(m, (f0 + U[3 * N + m * G + j]) / ((T)1 + U[2 * N + m * G + j]));
+          break;
+        case PK_ADV:
+          // u.grad G (Eq. gtilde-evol) or u.grad D
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const T ua = kin ? adv_x : U[m * G + j], va = kin ? adv_y : U[N + m * G + j];
-          put(m, ua * x[m].x + va * x[m].y);
-        }
-        break;
-      default: {
-        // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0.
-        // The gathered values go through the thread's own slots of S first,
-        // so that only a few of the bilinear loads are in flight per thread.
+          for (int m = 0; m < 8; ++m) {
+            const T ua = kin ? adv_x : U[m * G + j], va = kin ? adv_y : U[N + m * G + j];
+            put(m, ua * x[m].x + va * x[m].y);
+          }
+          break;
+        default: {
+          // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0.
+          // The gathered values go through the thread's own slots of S first,
+          // so that only a few of the bilinear loads are in flight per thread.
 #pragma unroll 1
-        for (int m = 0; m < 8; ++m) {
-          const int e = m * G + j;
-          const T xx = XI[e], xy = XI[N + e];
-          T fi;
-          if (kind == PK_XI && kin) fi = pc == 0 ? adv_x : adv_y;
-          else fi = bilinear<T>(d.phys + (long long)pc * g.np, e, y, xx, xy, inv_dx, N);
-          S[e] = fi;
-        }
+          for (int m = 0; m < 8; ++m) {
+            const int e = m * G + j;
+            const T xx = XI[e], xy = XI[N + e];
+            T fi;
+            if (kind == PK_XI && kin) fi = pc == 0 ? adv_x : adv_y;
+            else fi = bilinear<T>(d.phys + (long long)pc * g.np, e, y, xx, xy, inv_dx, N);
+            S[e] = fi;
+          }
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int e = m * G + j;
-          const T xx = XI[e], xy = XI[N + e];
-          const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
-          const T wx = s0 ? (T)0.5 * ua : xx * inv_s;
-          const T wy = s0 ? (T)0.5 * va : xy * inv_s;
-          const T wg = wx * x[m].x + wy * x[m].y;
-          const T fi = S[e];
-          put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wg : fi - wg);
+          for (int m = 0; m < 8; ++m) {
+            const int e = m * G + j;
+            const T xx = XI[e], xy = XI[N + e];
+            const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
+            const T wx = s0 ? (T)0.5 * ua : xx * inv_s;
+            const T wy = s0 ? (T)0.5 * va : xy * inv_s;
+            const T wgrad = wx * x[m].x + wy * x[m].y;
+            const T fi = S[e];
+            put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wgrad : fi - wgrad);
+          }
+          break;
         }
-        break;
       }
     }
-    if (slot == 0) pend = p;
-    slot ^= 1;
-    ++p;
-    if (slot == 0 || p == p1) {
-      cplx<T> z[8];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) z[m] = mk<T>(PZ[m * G + j], slot == 0 ? PZ[N + m * G + j] : (T)0);
-      group_fft<T, -1>(z, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
-      store_pair_spectrum<T>(z, buf0, buf1, w, d.pmix + (long long)pend * g.mi,
-                             slot == 0 ? d.pmix + (long long)(p - 1) * g.mi : nullptr, rowoff, j, G, grp, N, g.K,
-                             g.KXP);
-      slot = 0;
-    }
+    for (int m = 0; m < 8; ++m) x[m] = mk<T>(PZ[m * G + j], npq == 2 ? PZ[N + m * G + j] : (T)0);
+    group_fft<T, -1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    store_pair_spectrum<T>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
+                           npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, G, gi, N, g.K,
+                           g.KXP);
   }
 }
 
