@@ -54,6 +54,7 @@ struct sw_handle {
   int64_t steps_total = 0;
   Layout L{};
   // launch shapes: column tile 2^lC columns; row_prod Bp rows and ppb
+  // product pairs per block (0: automatic, see batch_build_t)
   // product pairs per block; row_inv Bi rows per block
   int lC = 2, Bp = 1, ppb = 1, Bi = 1;
   uint64_t version = 1;  // bumped whenever L or the launch shapes change
@@ -273,7 +274,7 @@ static void batch_free(BatchExec* b) {
 }
 
 template <typename T>
-static void fill_desc(sw_handle* h, RunDesc<T>& d) {
+static void fill_desc(sw_handle* h, RunDesc<T>& d, int ppb) {
   std::memset(&d, 0, sizeof(d));
   const Geom& g = h->g;
   d.g = g;
@@ -294,7 +295,7 @@ static void fill_desc(sw_handle* h, RunDesc<T>& d) {
   d.ticket = h->ticket;
   d.lC = h->lC;
   d.Bp = h->Bp;
-  d.ppb = h->ppb;
+  d.ppb = ppb;
   d.Wp = 1;
   d.Bi = h->Bi;
   const Layout& L = h->L;
@@ -303,7 +304,7 @@ static void fill_desc(sw_handle* h, RunDesc<T>& d) {
   d.nb[KT_COL_INV] = L.np > 0 ? ntile * L.ni : 0;
   d.nb[KT_ROW_INV] = (L.np > 0 && L.strategy == 2) ? 2 * (g.N / h->Bi) : 0;
   d.nb[KT_PHYS_Q] = (L.np > 0 && L.strategy == 2 && L.has_q) ? (int)((g.np + 255) / 256) : 0;
-  d.nb[KT_ROW_PROD] = L.np > 0 ? (g.N / h->Bp) * ((npairs + h->ppb - 1) / h->ppb) : 0;
+  d.nb[KT_ROW_PROD] = L.np > 0 ? (g.N / h->Bp) * ((npairs + ppb - 1) / ppb) : 0;
   d.nb[KT_COL_FWD] = L.np > 0 ? ntile * L.np : 0;
   d.nb[KT_UPDATE] = (int)((g.ms + 255) / 256) * L.nf;
 }
@@ -326,14 +327,17 @@ static int batch_build_t(BatchExec* b) {
   for (int r = 0; r < n; ++r) {
     const sw_handle* h = b->members[r];
     const int npairs = (h->L.np + 1) / 2;
-    const int npb = h->ppb < npairs ? h->ppb : npairs;
+    const int npb = (h->ppb == 0 || h->ppb > npairs) ? npairs : h->ppb;
     const int w = row_prod_groups<T>(h->g.N, h->Bp, npb, h->L.strategy);
     W = w < W ? w : W;
   }
   if (n == 0) W = 1;
   for (int r = 0; r < n; ++r) {
     sw_handle* h = b->members[r];
-    fill_desc<T>(h, descs[r]);
+    // automatic pairs per block: all of them when the row's groups share
+    // them out or the grid has rows enough to fill the GPU (N >= 1024), else
+    // one (the row's pairs spread over blocks)
+    fill_desc<T>(h, descs[r], h->ppb != 0 ? h->ppb : ((W > 1 || h->g.N >= 1024) ? MAXP : 1));
     descs[r].Wp = W;
     const RunDesc<T>& d = descs[r];
     const int N = h->g.N;
@@ -748,7 +752,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   h->Bp = row_block_rows(g.N);
   h->Bi = row_block_rows(g.N);
   // all product pairs per block: the row's groups share them out
-  h->ppb = MAXP;
+  h->ppb = 0;  // automatic (batch_build_t)
   const ArenaPlan A = plan_arena(g, h->tsz);
   const size_t o_y = A.o[0], o_ys = A.o[1], o_ys2 = A.o[2], o_acc = A.o[3], o_comp = A.o[4], o_ps = A.o[5];
   const size_t o_mix = A.o[6], o_pmix = A.o[7], o_phys = A.o[8], o_ef = A.o[9], o_tw = A.o[10];

@@ -26,14 +26,20 @@ template <typename T> size_t row_prod_smem(int N, int B, int W, int strategy) {
 
 // Largest W for B rows and npb product pairs per block: W > 1 needs whole
 // warps per group (N >= 256), a thread count within the block limit, at most
-// 15 named barriers (groups of N >= 512) and 200 KB of shared memory.
+// 15 named barriers (groups of N >= 512) and at most 110 KB of shared memory
+// (two blocks per SM; one resident block per SM made the wider shape slower).
 template <typename T> int row_prod_groups(int N, int B, int npb, int strategy) {
   const int G = N / 8;
   if (G < 32) return 1;
   int W = npb < 1 ? 1 : npb;
   while (W > 1 && (B * W * G > row_prod_max_threads<T>() || (G >= 64 && B * W > 15) ||
-                   row_prod_smem<T>(N, B, W, strategy) > (size_t)200 * 1024))
+                   row_prod_smem<T>(N, B, W, strategy) > (size_t)110 * 1024))
     --W;
+  // Strategy 2 transforms one base pair (xi) before the products, so the
+  // row's other groups wait at the barrier; that pays only when every pair
+  // gets a group of its own (measured slower at 1024^2 with 2 groups for 6
+  // pairs)
+  if (strategy == 2 && W < npb) W = 1;
   return W;
 }
 
