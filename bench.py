@@ -362,6 +362,32 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1
                         "strategy 1 or 2, FP32, 150 GB budget, %d requests" % n_jobs}
 
 
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of this
+# bench's timed region (profiles/traffic_rowprod_bench256.md: mean of the warm
+# launches); valid only while the kernel sources are those of that capture.
+TRAFFIC_CAPTURE = {"kernel": "row_prod", "bytes": 228900.0,
+                   "sources_sha256": "3dfda3670cec127fea28bd66d9f62906867e9e73f4ccc9c821c4a4ec7381da18"}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    root = os.path.join(ROOT, "paper_2208_02682_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(root)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(root, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    c = TRAFFIC_CAPTURE
+    if kernel != c["kernel"] or kernel_sources_sha256() != c["sources_sha256"]:
+        return None
+    return c["bytes"]
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -460,7 +486,7 @@ def run_ours(args):
     peak, peak_src = peaks()
     achieved = (byt / cnt) / (t_ms / cnt * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "frac": achieved / peak, "traffic": measured_traffic(dom), "kernel": dom,
                 "peak_source": peak_src,
                 "note": "256^2 working set is L2-resident; see DESIGN.md for the 1024^2 figures"}
     kernel_share = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / tot,
