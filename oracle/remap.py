@@ -1,4 +1,5 @@
-"""Strategy-1 remap to the mean-position grid (test infrastructure).
+"""Strategy-1 remap to the mean-position grid, and fields at lifted
+positions (test infrastructure).
 
 TEST INFRASTRUCTURE ONLY: used by tests/ (and bench.py's cpu_baseline leg),
 never by the product path.  Shares no code with the CUDA library.
@@ -77,3 +78,43 @@ def remap_strategy1(ftilde, pos_x, pos_y, iters=20):
         xi_x, xi_y = nx, ny
     fbar = {k: bilinear_at_displacement(v, xi_x, xi_y) for k, v in ftilde.items()}
     return fbar, X + xi_x, Y + xi_y, resid
+
+
+def lift(fields, pos_x, pos_y):
+    """Fields evaluated at given positions, f(Xi(x)), by the bilinear rule.
+
+    With Xi the Strategy-2 lift map (Sec. 3.2; Xi = x + xi), this gives the
+    instantaneous field at the particles' positions: Sec. 4.2.2 forms the
+    Lagrangian perturbation fbar^L(x) - f(x + xi(x, tau+T), tau+T), and
+    Sec. 4.2.1 notes that the Lagrangian mean PV is the rearrangement
+    qbar^L(x) = q(Xi(x), t).
+    """
+    N = pos_x.shape[0]
+    X, Y = grid(N)
+    return {k: bilinear_at_displacement(v, pos_x - X, pos_y - Y) for k, v in fields.items()}
+
+
+def shells(N):
+    """Number of wavenumber shells of the 2/3 box: round(sqrt(2) K) + 1."""
+    K = (N - 1) // 3
+    return int(np.floor(np.sqrt(2.0) * K + 0.5)) + 1
+
+
+def spectrum(f):
+    """Shell-summed spectrum of a real field on the 2/3 box (Sec. 4.2.2's
+    enstrophy spectra when f is the vorticity).
+
+    F = FFT(f)/N^2, kept for |kx|, |ky| <= K; shell n = round(|k|) collects
+    |F(k)|^2 / 2 over the whole plane, so the shells sum to half the mean
+    square of the box-limited field (Parseval).
+    """
+    N = f.shape[0]
+    K = (N - 1) // 3
+    F = np.fft.fft2(f) / (N * N)
+    k = np.fft.fftfreq(N, 1.0 / N)
+    KX, KY = np.meshgrid(k, k)
+    box = (np.abs(KX) <= K) & (np.abs(KY) <= K)
+    sh = np.floor(np.sqrt(KX * KX + KY * KY) + 0.5).astype(np.int64)
+    out = np.zeros(shells(N))
+    np.add.at(out, sh[box], 0.5 * np.abs(F[box]) ** 2)
+    return out
