@@ -319,6 +319,54 @@ def measure_remap(lm, torch, outs, strategies, iters=20):
     return res
 
 
+def measure_diagnostics(lm, torch, outs, strategies):
+    """Sec. 4.2.2's diagnostics on the bench interval: the Strategy-2 lift of
+    the four fields (lmean_lift at Xi, against each Lagrangian mean: the
+    Lagrangian perturbation), timed at 256^2 and on a 1024^2 map, and the
+    shell spectrum (sw_spectrum, synchronous) of a 256^2 field."""
+    s2 = outs[strategies.index(2)]
+    N = s2["pos_x"].shape[0]
+    fields = {k: s2[k] for k in FIELDS}
+
+    def timed_lift(px, py, f, reps=20):
+        for _ in range(3):
+            lm.lmean_lift(px, py, f)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            lm.lmean_lift(px, py, f)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {"lift_ms": {str(N): timed_lift(s2["pos_x"], s2["pos_y"], fields)}}
+    M = 1024
+    rng = np.random.Generator(np.random.PCG64(2048))
+    xm = 2 * np.pi * np.arange(M) / M
+    XM, YM = np.meshgrid(xm, xm)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    px = dev(XM + 0.2 * np.sin(YM) + 0.05 * si.random_smooth_field(M, 3, rng))
+    py = dev(YM + 0.2 * np.cos(XM) + 0.05 * si.random_smooth_field(M, 3, rng))
+    res["lift_ms"][str(M)] = timed_lift(px, py, {k: dev(si.random_smooth_field(M, 8, rng)) for k in FIELDS})
+    res["lift_grid_points_per_s"] = {k: int(k) ** 2 / (v * 1e-3) for k, v in res["lift_ms"].items()}
+    w = si.WORKLOADS["plain-256"]
+    h = lm.sw_create(lm.make_params(N, w.dt, precision="f32", nu8=w.nu8),
+                     np.ascontiguousarray(np.stack(w.initial_condition())))
+    f = s2["zeta"].contiguous()
+    lm.sw_spectrum(h, f, N)
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        spec = lm.sw_spectrum(h, f, N)
+    res["spectrum_ms_256"] = (time.perf_counter() - t0) / reps * 1e3
+    res["lagrangian_mean_zeta_enstrophy_spectrum_first_shells"] = [float(x) for x in spec[:8]]
+    lm.sw_destroy(h)
+    res["workload"] = ("bench interval's Strategy-2 outputs (lift of zeta, h, u, v at Xi; spectrum of the "
+                       "Lagrangian mean vorticity), and a 1024^2 smooth map with four fields; FP64")
+    return res
+
+
 def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
     """Poisson stream of Lagrangian-mean requests through sw_server."""
     import time as _t
@@ -531,6 +579,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["remap"] = measure_remap(lm, torch, outs, list(w.strategies))
+        extras["diagnostics"] = measure_diagnostics(lm, torch, outs, list(w.strategies))
         extras["batched"] = measure_batched(lm, torch)
         extras["precision_form"] = measure_precision(lm, torch)
         extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)

@@ -384,12 +384,44 @@ int sw_project_static(const double* in, double* out, int N, void* stream);
 int lmean_remap(int N, const double* pos_x, const double* pos_y, int nfields, const double* const* ftilde,
                 double* const* fbar, int iters, double* xi_x, double* xi_y, double* resid, void* stream);
 
+/* ---- diagnostics ------------------------------------------------------------
+ * Fields at given positions: out_k(y) = f_k(pos(y)) for every grid point y,
+ * by the periodic bilinear rule of the Strategy-2 solver (Sec. 4.2.1; cell
+ * index i + floor((pos - y)/dx), weight the remainder), every FP64 operation
+ * separately rounded.  With pos = Xi, the lift map that lmean_end returns
+ * for Strategy 2 (Sec. 3.2), this gives f(x + xi(x, tau+T), tau+T): the
+ * Lagrangian perturbation of Sec. 4.2.2 is fbar^L minus the lifted
+ * instantaneous field, and Sec. 4.2.1's rearrangement qbar^L(x) = q(Xi(x))
+ * compares the lifted PV with its Lagrangian mean.
+ *   N:            power of two in [16, 4096].
+ *   pos_x, pos_y: device, N*N doubles each (row-major, y slow), absolute
+ *                 (unwrapped) positions.
+ *   nfields:      1..LM_REMAP_MAX_FIELDS.
+ *   f, out:       HOST arrays of nfields device pointers, N*N doubles each;
+ *                 no output may alias an input or another output.
+ *   stream:       cudaStream_t (NULL: legacy default stream); asynchronous.
+ * Errors: SW_EINVAL (message via sw_last_error(NULL)), SW_ECUDA. */
+int lmean_lift(int N, const double* pos_x, const double* pos_y, int nfields, const double* const* f,
+               double* const* out, void* stream);
+
+/* Shell spectrum of a real N*N field on the handle's 2/3 box (Sec. 4.2.2
+ * plots enstrophy spectra: pass the vorticity).  With F = FFT(f)/N^2 kept for
+ * |kx|, |ky| <= K, shell n = round(|k|) receives sum |F(k)|^2/2 over the
+ * whole plane, so the shells sum to half the mean square of the box-limited
+ * field.  Uses the handle's FP64 staging buffers and stream (the dynamic and
+ * Lagrangian-mean state is not touched); synchronises.
+ *   field:     N*N doubles, host (on_device = 0) or device (on_device = 1).
+ *   spectrum:  HOST array of nshell doubles; nshell >= round(sqrt(2) K) + 1
+ *              (K = floor((N-1)/3)); entries past that count are set to 0.
+ * Errors: SW_EINVAL, SW_ECUDA (message via sw_last_error(h)). */
+int sw_spectrum(sw_handle* h, const double* field, int on_device, double* spectrum, int nshell);
+
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);
 
 /* Message for the last failing call on h ("" if none); valid until the next
  * call on h.  With h == NULL, the message of the last failing sw_create,
- * sw_project_static or lmean_remap on the calling thread. */
+ * sw_project_static, lmean_remap or lmean_lift on the calling thread. */
 const char* sw_last_error(sw_handle* h);
 
 /* Library version string. */

@@ -29,7 +29,8 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "sw_launch_count", "sw_project_static", "sw_batch_create", "sw_batch_step",
            "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
            "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
-           "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap")
+           "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap", "lmean_lift",
+           "sw_spectrum")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
         "sw_project_static": (C.c_int, [_DP, _DP, C.c_int, C.c_void_p]),
         "lmean_remap": (C.c_int, [C.c_int, _DP, _DP, C.c_int, C.POINTER(_DP), C.POINTER(_DP), C.c_int, _DP, _DP,
                                   _DP, C.c_void_p]),
+        "lmean_lift": (C.c_int, [C.c_int, _DP, _DP, C.c_int, C.POINTER(_DP), C.POINTER(_DP), C.c_void_p]),
+        "sw_spectrum": (C.c_int, [C.c_void_p, _DP, C.c_int, _DP, C.c_int]),
         "sw_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(H)]),
         "sw_batch_step": (C.c_int, [H, C.c_int64]),
         "sw_batch_tune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
@@ -472,6 +475,49 @@ def lmean_remap(pos_x, pos_y, ftilde, iters=20, xi=True, resid=True, stream=None
                          C.c_void_p(stream or 0))
     if rc != SW_OK:
         raise SWError(rc, lib.sw_last_error(None).decode())
+    return out
+
+
+def lmean_lift(pos_x, pos_y, fields, stream=None):
+    """Fields at given positions (see include/lagmean.h): dict name -> f(pos)
+    for contiguous float64 CUDA tensors of shape (N, N)."""
+    import torch
+
+    N = int(pos_x.shape[-1])
+    names = list(fields)
+    out = {k: torch.empty_like(pos_x) for k in names}
+    px, dx_ = _ptr(pos_x)
+    py, dy_ = _ptr(pos_y)
+    if not (dx_ and dy_):
+        raise ValueError("lmean_lift takes device tensors")
+    fin = (_DP * max(1, len(names)))()
+    fout = (_DP * max(1, len(names)))()
+    for i, k in enumerate(names):
+        p, d = _ptr(fields[k])
+        if not d or tuple(fields[k].shape) != (N, N):
+            raise ValueError("fields must be (N, N) float64 CUDA tensors")
+        fin[i] = p
+        fout[i] = _ptr(out[k])[0]
+    lib = load()
+    rc = lib.lmean_lift(N, px, py, len(names), fin, fout, C.c_void_p(stream or 0))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return out
+
+
+def spectrum_shells(N):
+    """Number of shells sw_spectrum fills for an N x N grid."""
+    K = (int(N) - 1) // 3
+    return int(np.floor(np.sqrt(2.0) * K + 0.5)) + 1
+
+
+def sw_spectrum(h, field, N):
+    """Shell spectrum of a real N x N field (numpy array or CUDA tensor) on the
+    handle's 2/3 box; returns a numpy array of spectrum_shells(N) values."""
+    p, d = _ptr(field)
+    n = spectrum_shells(N)
+    out = np.zeros(n)
+    _check(load().sw_spectrum(h, p, d, out.ctypes.data_as(_DP), n), h)
     return out
 
 

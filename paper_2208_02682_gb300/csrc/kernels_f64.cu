@@ -64,6 +64,27 @@ __global__ void k_add_real(double2* p, double delta) {
   if (threadIdx.x == 0 && blockIdx.x == 0) p->x += delta;
 }
 
+// Shell sums of |F|^2/2 over the whole plane from the kx >= 0 half of the
+// 2/3 box (FP64 spectral layout [ky + K][kx], row stride KXP): shell
+// round(|k|), weight 2 for kx > 0 (the mirrored half).
+__global__ void k_spectrum_shells(const double2* __restrict__ F, int K, int KXP, double* __restrict__ acc) {
+  const int NY = 2 * K + 1;
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (long long)NY * KXP) return;
+  const int kyi = (int)(m / KXP), kx = (int)(m - (long long)kyi * KXP);
+  if (kx > K) return;
+  const int ky = kyi - K;
+  const int sh = (int)floor(sqrt((double)(kx * kx + ky * ky)) + 0.5);
+  const double2 v = F[m];
+  atomicAdd(acc + sh, (kx == 0 ? 0.5 : 1.0) * (v.x * v.x + v.y * v.y));
+}
+
+cudaError_t launch_spectrum_shells(const double2* F, int K, int KXP, double* acc, cudaStream_t s) {
+  const long long n = (long long)(2 * K + 1) * KXP;
+  k_spectrum_shells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F, K, KXP, acc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s) {
   k_add_real<<<1, 1, 0, s>>>(p, delta);
   return cudaGetLastError();

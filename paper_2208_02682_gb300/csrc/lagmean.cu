@@ -1106,6 +1106,49 @@ extern "C" int sw_set_state(sw_handle* h, const void* blob, size_t size) {
   return SW_OK;
 }
 
+extern "C" int sw_spectrum(sw_handle* h, const double* field, int on_device, double* spectrum, int nshell) {
+  if (!h) return SW_EINVAL;
+  h->err.clear();
+  if (!field || !spectrum) return fail(h, SW_EINVAL, "field and spectrum are required");
+  const Geom& g = h->g;
+  const int ns = (int)std::floor(std::sqrt(2.0) * g.K + 0.5) + 1;
+  if (nshell < ns)
+    return fail(h, SW_EINVAL, "nshell must be at least round(sqrt(2) K) + 1 = " + std::to_string(ns));
+  cudaStream_t s = h->stream;
+  // the field into the FP64 staging slot 0, forward 2D transform into the
+  // spectral staging slot 0 (the path of an initial condition), shell sums
+  // into staging slot 1
+  CK(h, cudaMemcpyAsync(h->out64, field, (size_t)g.np * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  RowFwdArgs<double> rf;
+  std::memset(&rf, 0, sizeof(rf));
+  rf.src = h->out64;
+  rf.dst = h->mix64;
+  rf.tw = h->tw64;
+  rf.g = g;
+  rf.B = h->Bi;
+  rf.npairs = 1;
+  rf.a_idx[0] = 0; rf.b_idx[0] = -1; rf.oa[0] = 0; rf.ob[0] = -1;
+  CK(h, launch_row_fwd<double>(rf, s));
+  ColFwdArgs<double> cf;
+  cf.src = h->mix64;
+  cf.dst = h->spec64;
+  cf.tw = h->tw64;
+  cf.g = g;
+  cf.nout = 1;
+  cf.src_idx[0] = cf.dst_idx[0] = 0;
+  CK(h, launch_col_fwd<double>(cf, s));
+  double* acc = h->out64 + g.np;
+  CK(h, cudaMemsetAsync(acc, 0, (size_t)ns * sizeof(double), s));
+  CK(h, launch_spectrum_shells(h->spec64, g.K, g.KXP, acc, s));
+  h->launches += 3;
+  std::vector<double> tmp(ns);
+  CK(h, cudaMemcpyAsync(tmp.data(), acc, (size_t)ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  for (int k = 0; k < nshell; ++k) spectrum[k] = k < ns ? tmp[k] : 0.0;
+  return SW_OK;
+}
+
 extern "C" int sw_kernel_times(sw_handle* h, int64_t nsteps, double ms[SW_K_COUNT], int64_t launches[SW_K_COUNT],
                                double bytes[SW_K_COUNT]) {
   if (!h) return SW_EINVAL;

@@ -57,6 +57,7 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
 cudaError_t launch_diag(const double* phys, long long np, double f0, double c2, double* part, int nblk,
                         double* out, cudaStream_t s);
 cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s);
+cudaError_t launch_spectrum_shells(const double2* F, int K, int KXP, double* acc, cudaStream_t s);
 
 #ifdef LM_INSTANTIATE
 // Raise the dynamic shared-memory limit of every kernel once (outside any

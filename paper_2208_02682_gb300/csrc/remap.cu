@@ -1,5 +1,7 @@
 // remap.cu -- lmean_remap: Strategy-1 means onto the mean-position grid,
-// Sec. 3.1, Eq. (remap-strat1), through the lift map Xi = (Xi^{-1})^{-1}.
+// Sec. 3.1, Eq. (remap-strat1), through the lift map Xi = (Xi^{-1})^{-1};
+// lmean_lift: fields evaluated at given positions (the lift map of
+// Strategy 2, Sec. 3.2), for the diagnostics of Secs. 4.2.1-4.2.2.
 //
 // One thread per grid point y = (x_i, y_j):
 //   xi = 0; repeat iters times: xi <- d_I(y + xi),  d = x - Xi^{-1}(x)
@@ -108,8 +110,43 @@ __global__ void __launch_bounds__(256) k_remap(const __grid_constant__ RemapArgs
   if (a.resid) a.resid[idx] = r;
 }
 
+struct LiftArgs {
+  const double* pos_x;
+  const double* pos_y;
+  const double* f[LM_REMAP_MAX_FIELDS];
+  double* out[LM_REMAP_MAX_FIELDS];
+  int N, log2N, nf;
+};
+
+// out(y) = f_I(pos(y)), the displacement pos - y taken from the grid point
+// (same rounding steps as the remap's final interpolation)
+__global__ void __launch_bounds__(256) k_lift(const __grid_constant__ LiftArgs a) {
+  extern __shared__ double xs[];
+  const int N = a.N;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) xs[t] = coord(t, N);
+  __syncthreads();
+  const long long np = (long long)N * N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= np) return;
+  const int i = (int)(idx & (N - 1)), j = (int)(idx >> a.log2N);
+  const double inv_dx = __ddiv_rn((double)N, kTwoPi);
+  const double xx = __dsub_rn(a.pos_x[idx], xs[i]), xy = __dsub_rn(a.pos_y[idx], xs[j]);
+  const Cell c = cell_of(i, j, __dmul_rn(xx, inv_dx), __dmul_rn(xy, inv_dx), N);
+  const long long o00 = (long long)c.j0 * N + c.i0, o01 = (long long)c.j0 * N + c.i1;
+  const long long o10 = (long long)c.j1 * N + c.i0, o11 = (long long)c.j1 * N + c.i1;
+  for (int f = 0; f < a.nf; ++f) {
+    const double* F = a.f[f];
+    a.out[f][idx] = blend(c, F[o00], F[o01], F[o10], F[o11]);
+  }
+}
+
 int fail(const std::string& m, int rc) {
   lm::set_handleless_error("lmean_remap: " + m);
+  return rc;
+}
+
+int fail_lift(const std::string& m, int rc) {
+  lm::set_handleless_error("lmean_lift: " + m);
   return rc;
 }
 
@@ -163,5 +200,37 @@ extern "C" int lmean_remap(int N, const double* pos_x, const double* pos_y, int 
   k_remap<<<blocks, 256, (size_t)N * sizeof(double), (cudaStream_t)stream>>>(a);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(std::string("launch: ") + cudaGetErrorString(e), SW_ECUDA);
+  return SW_OK;
+}
+
+extern "C" int lmean_lift(int N, const double* pos_x, const double* pos_y, int nfields, const double* const* f,
+                          double* const* out, void* stream) {
+  if (N < 16 || N > 4096 || (N & (N - 1)) != 0) return fail_lift("N must be a power of two in [16, 4096]", SW_EINVAL);
+  if (!pos_x || !pos_y) return fail_lift("pos_x and pos_y are required", SW_EINVAL);
+  if (nfields < 1 || nfields > LM_REMAP_MAX_FIELDS)
+    return fail_lift("nfields must be in [1, " + std::to_string(LM_REMAP_MAX_FIELDS) + "]", SW_EINVAL);
+  if (!f || !out) return fail_lift("f and out arrays are required", SW_EINVAL);
+  LiftArgs a = {};
+  a.pos_x = pos_x;
+  a.pos_y = pos_y;
+  a.N = N;
+  while ((1 << a.log2N) < N) ++a.log2N;
+  a.nf = nfields;
+  for (int k = 0; k < nfields; ++k) {
+    if (!f[k] || !out[k]) return fail_lift("null field pointer", SW_EINVAL);
+    a.f[k] = f[k];
+    a.out[k] = out[k];
+  }
+  // an output may not be an input (neighbouring points are gathered while
+  // outputs are written) nor another output
+  for (int k = 0; k < nfields; ++k) {
+    if (out[k] == pos_x || out[k] == pos_y) return fail_lift("an output aliases an input", SW_EINVAL);
+    for (int m = 0; m < nfields; ++m)
+      if (out[k] == f[m] || (m > k && out[k] == out[m])) return fail_lift("an output aliases another buffer", SW_EINVAL);
+  }
+  const long long np = (long long)N * N;
+  k_lift<<<(unsigned)((np + 255) / 256), 256, (size_t)N * sizeof(double), (cudaStream_t)stream>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_lift(std::string("launch: ") + cudaGetErrorString(e), SW_ECUDA);
   return SW_OK;
 }

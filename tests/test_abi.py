@@ -120,3 +120,37 @@ def test_remap_arguments_rejected_before_device_use(lm, case):
     rc = lib.lmean_remap(N, pos_x, pos_y, nf, fin, fout, iters, xi_x, None, None, None)
     assert rc == lm.api.SW_EINVAL
     assert "lmean_remap" in lm.sw_last_error(None)
+
+
+@pytest.mark.parametrize("case", ["N_not_pow2", "no_fields", "too_many_fields", "alias_pos", "alias_field",
+                                  "null_pos"])
+def test_lift_arguments_rejected_before_device_use(lm, case):
+    # every case is invalid: the call returns before touching the (fake)
+    # device addresses or launching anything
+    lib = lm.api.load()
+    DP = lm.api._DP
+    fake = [C.cast(C.c_void_p(0x10000 * (k + 1)), DP) for k in range(6)]
+    N, nf = 64, 1
+    pos_x, pos_y = fake[0], fake[1]
+    fin = (DP * 1)(fake[2])
+    fout = (DP * 1)(fake[3])
+    if case == "N_not_pow2":
+        N = 100
+    elif case == "no_fields":
+        nf = 0
+    elif case == "too_many_fields":
+        nf = 17
+    elif case == "alias_pos":
+        fout = (DP * 1)(fake[0])
+    elif case == "alias_field":
+        fout = (DP * 1)(fake[2])
+    elif case == "null_pos":
+        pos_x = None
+    assert lib.lmean_lift(N, pos_x, pos_y, nf, fin, fout, None) == lm.api.SW_EINVAL
+    assert "lmean_lift" in lm.sw_last_error(None)
+
+
+def test_spectrum_rejects_null_handle(lm):
+    lib = lm.api.load()
+    out = np.zeros(4)
+    assert lib.sw_spectrum(None, None, 0, out.ctypes.data_as(lm.api._DP), 4) == lm.api.SW_EINVAL
