@@ -367,6 +367,37 @@ def measure_diagnostics(lm, torch, outs, strategies):
     return res
 
 
+def measure_semi_lagrangian(lm, torch, outs, strategies):
+    """App. B's semi-Lagrangian Strategy 1 (trapezoid, cubic) over the bench
+    interval on FP32 dynamics: grid-point-steps/s of the coupled stepping
+    (sw_step + FP64 physical fields + the update, per step), and its means
+    remapped (Eq. remap-strat1) against the bench's Strategy-2 means."""
+    w = si.WORKLOADS["plain-256"]
+    N, n = w.N, w.n_steps
+    h = lm.sw_create(lm.make_params(N, w.dt, precision="f32", nu8=w.nu8),
+                     np.ascontiguousarray(np.stack(w.initial_condition())))
+    s = lm.sw_sl_create(h, lm.make_sl_params(FIELDS, pos=True, scheme="trapezoid", interp="cubic", n_steps=n))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lm.sw_sl_step(s, n)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {k: torch.empty((N, N), dtype=torch.float64, device="cuda") for k in FIELDS + ("pos_x", "pos_y")}
+    lm.sw_sl_end(s, out)
+    lm.sw_destroy(h)
+    r = lm.lmean_remap(out["pos_x"], out["pos_y"], {k: out[k] for k in FIELDS}, iters=20)
+    s2 = outs[strategies.index(2)]
+    agree = {}
+    for k in FIELDS:
+        a, b = r[k].cpu().numpy(), s2[k].cpu().numpy()
+        agree[k] = float(np.linalg.norm(a - b) / np.linalg.norm(b - b.mean()))
+    return {"ms_per_interval": ms, "grid_point_steps_per_s": N * N * n / (ms * 1e-3),
+            "remapped_vs_strategy2_rel_l2": agree,
+            "workload": "plain-256 interval, FP32 dynamics, trapezoid + cubic interpolation, FP64 means"}
+
+
 def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
     """Poisson stream of Lagrangian-mean requests through sw_server."""
     import time as _t
@@ -412,20 +443,24 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1
 
 # DRAM bytes per launch of the dominant kernel, from one ncu capture of this
 # bench's timed region (profiles/traffic_rowprod_bench256.md: mean of the warm
-# launches); valid only while the kernel sources are those of that capture.
+# launches); valid only while the stage-kernel sources are those of that
+# capture (the hash is refreshed with each capture).
 TRAFFIC_CAPTURE = {"kernel": "row_prod", "bytes": 228900.0,
                    "sources_sha256": "3dfda3670cec127fea28bd66d9f62906867e9e73f4ccc9c821c4a4ec7381da18"}
+
+
+# the sources that define the stage kernels and their launch shapes
+STAGE_SOURCES = ("common.cuh", "fft.cuh", "kernels.cuh", "stage.cuh", "launch.cuh", "kernels_f32.cu", "lagmean.cu")
 
 
 def kernel_sources_sha256():
     import hashlib
     root = os.path.join(ROOT, "paper_2208_02682_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(root)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode())
-            with open(os.path.join(root, f), "rb") as fh:
-                h.update(fh.read())
+    for f in STAGE_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
@@ -580,6 +615,7 @@ def run_ours(args):
     if not args.no_extras:
         extras["remap"] = measure_remap(lm, torch, outs, list(w.strategies))
         extras["diagnostics"] = measure_diagnostics(lm, torch, outs, list(w.strategies))
+        extras["semi_lagrangian"] = measure_semi_lagrangian(lm, torch, outs, list(w.strategies))
         extras["batched"] = measure_batched(lm, torch)
         extras["precision_form"] = measure_precision(lm, torch)
         extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)

@@ -416,6 +416,56 @@ int lmean_lift(int N, const double* pos_x, const double* pos_y, int nfields, con
  * Errors: SW_EINVAL, SW_ECUDA (message via sw_last_error(h)). */
 int sw_spectrum(sw_handle* h, const double* field, int on_device, double* spectrum, int nshell);
 
+/* ---- semi-Lagrangian Strategy 1 (App. B) ---------------------------------
+ * The grid-based Lagrangian average as a semi-Lagrangian discretisation of
+ * Eqs. (gtilde-evol) and (Xi-1evol) (App. B): after every RK4 step of the
+ * handle's dynamics, at each grid point X with departure point
+ * Y = X - dt u(X, t_{n+1}),
+ *   SL_EULER      g(X) = g_I(Y) + dt f(X, t_{n+1})              Eq. (sdiscrete_gtilde)
+ *   SL_TRAPEZOID  g(X) = g_I(Y) + dt [f_I(Y, t_n) + f(X, t_{n+1})]/2
+ *                                                    Eq. (sdiscrete_gtilde_trapez)
+ * for g = (t - tau) f~, and the mean positions by the same rule applied to
+ * f = x (Eq. (sdiscrete_Xi-1) for the trapezoid), carried as the periodic
+ * displacement D = (t - tau)(x - Xi^{-1}).  _I: interpolation at Y,
+ * SL_LINEAR (bilinear) or SL_CUBIC (tensor-product 4-point Lagrange; the
+ * paper does not name its cubic scheme).  u is the flow velocity (the
+ * constant adv for the kinematic model).  FP64 on physical grid fields,
+ * whatever the handle's precision.  Results: f~^L = g/T and
+ * Xi^{-1}(x, tau+T) = x - D/T (feed them to lmean_remap for fbar^L). */
+#define SL_EULER 0
+#define SL_TRAPEZOID 1
+#define SL_LINEAR 0
+#define SL_CUBIC 1
+typedef struct sl_params {
+  int32_t fields;   /* LM_ZETA | LM_H | LM_U | LM_V | LM_Q | LM_POS (nonzero) */
+  int32_t scheme;   /* SL_EULER or SL_TRAPEZOID */
+  int32_t interp;   /* SL_LINEAR or SL_CUBIC */
+  int32_t reserved; /* must be 0 */
+  int64_t n_steps;  /* T = n_steps * dt, >= 1 */
+} sl_params;
+typedef struct sl_interval sl_interval;
+
+/* Open an interval at the handle's current time.  The handle must have no
+ * open lmean interval; while the SL interval lives, step the handle only
+ * through sw_sl_step and do not destroy it.  Allocates the interval's device
+ * buffers (about 2 (2 nf + 2) N*N doubles for nf averaged fields) and
+ * synchronises.  Errors: SW_EINVAL, SW_EBUSY, SW_ENOMEM, SW_ECUDA (message
+ * via sw_last_error(h), or sw_last_error(NULL) when h is NULL). */
+int sw_sl_create(sw_handle* h, const sl_params* p, sl_interval** out);
+
+/* Advance the dynamics and the interval by nsteps >= 0 steps (one sw_step
+ * and one update each); SW_ERANGE if more than remain.  Asynchronous. */
+int sw_sl_step(sl_interval* s, int64_t nsteps);
+
+/* Requires the interval complete (SW_ESTATE otherwise).  Writes f~^L into
+ * the zeta/h/u/v/q pointers of out and Xi^{-1} into pos_x/pos_y for the
+ * requested fields (N*N doubles each; e_* ignored; host or device per
+ * out->on_device), then frees the interval.  Synchronises. */
+int sw_sl_end(sl_interval* s, const lm_result* out);
+
+/* Free an interval without results.  NULL: no-op. */
+void sw_sl_destroy(sl_interval* s);
+
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);
 

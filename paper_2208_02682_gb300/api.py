@@ -30,7 +30,7 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
            "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
            "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap", "lmean_lift",
-           "sw_spectrum")
+           "sw_spectrum", "sw_sl_create", "sw_sl_step", "sw_sl_end", "sw_sl_destroy")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -55,6 +55,15 @@ class lm_result(C.Structure):
                 ("pos_x", _DP), ("pos_y", _DP),
                 ("e_zeta", _DP), ("e_h", _DP), ("e_u", _DP), ("e_v", _DP), ("e_q", _DP),
                 ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+SL_EULER, SL_TRAPEZOID = 0, 1
+SL_LINEAR, SL_CUBIC = 0, 1
+
+
+class sl_params(C.Structure):
+    _fields_ = [("fields", C.c_int32), ("scheme", C.c_int32), ("interp", C.c_int32),
+                ("reserved", C.c_int32), ("n_steps", C.c_int64)]
 
 
 class sw_server_params(C.Structure):
@@ -119,6 +128,10 @@ def load(path: str = LIB_PATH):
                                   _DP, C.c_void_p]),
         "lmean_lift": (C.c_int, [C.c_int, _DP, _DP, C.c_int, C.POINTER(_DP), C.POINTER(_DP), C.c_void_p]),
         "sw_spectrum": (C.c_int, [C.c_void_p, _DP, C.c_int, _DP, C.c_int]),
+        "sw_sl_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+        "sw_sl_step": (C.c_int, [C.c_void_p, C.c_int64]),
+        "sw_sl_end": (C.c_int, [C.c_void_p, C.c_void_p]),
+        "sw_sl_destroy": (None, [C.c_void_p]),
         "sw_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(H)]),
         "sw_batch_step": (C.c_int, [H, C.c_int64]),
         "sw_batch_tune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
@@ -519,6 +532,56 @@ def sw_spectrum(h, field, N):
     out = np.zeros(n)
     _check(load().sw_spectrum(h, p, d, out.ctypes.data_as(_DP), n), h)
     return out
+
+
+def make_sl_params(fields=("zeta", "h", "u", "v"), pos=True, scheme="trapezoid", interp="cubic",
+                   n_steps=1) -> sl_params:
+    p = sl_params()
+    mask = 0
+    for f in fields:
+        mask |= FIELD_BITS[f]
+    if pos:
+        mask |= LM_POS
+    p.fields = mask
+    p.scheme = {"euler": SL_EULER, "trapezoid": SL_TRAPEZOID}[scheme]
+    p.interp = {"linear": SL_LINEAR, "cubic": SL_CUBIC}[interp]
+    p.reserved = 0
+    p.n_steps = int(n_steps)
+    return p
+
+
+def sw_sl_create(h, p: sl_params):
+    """Open a semi-Lagrangian Strategy-1 interval on handle h (App. B; see
+    include/lagmean.h); returns the interval."""
+    s = C.c_void_p()
+    _check(load().sw_sl_create(h, C.byref(p), C.byref(s)), h)
+    return (s, h)
+
+
+def sw_sl_step(s, nsteps):
+    _check(load().sw_sl_step(s[0], int(nsteps)), s[1])
+
+
+def sw_sl_end(s, out: dict):
+    """out: dict key -> array among zeta, h, u, v, q, pos_x, pos_y; all host or
+    all device.  Frees the interval."""
+    r = lm_result()
+    ondev = set()
+    for k in ("zeta", "h", "u", "v", "q", "pos_x", "pos_y"):
+        a = out.get(k)
+        p, d = _ptr(a)
+        if a is not None:
+            ondev.add(d)
+            setattr(r, k, p)
+    if len(ondev) > 1:
+        raise ValueError("outputs must be all host or all device")
+    r.on_device = ondev.pop() if ondev else 0
+    _check(load().sw_sl_end(s[0], C.byref(r)), s[1])
+    return out
+
+
+def sw_sl_destroy(s):
+    load().sw_sl_destroy(s[0])
 
 
 def sw_last_error(h=None):

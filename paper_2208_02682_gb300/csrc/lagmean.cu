@@ -970,11 +970,9 @@ extern "C" int sw_set_fields(sw_handle* h, const double* uvh, int on_device) {
   return SW_OK;
 }
 
-extern "C" int sw_diag(sw_handle* h, double out[3]) {
-  if (!h) return SW_EINVAL;
-  h->err.clear();
-  if (!out) return fail(h, SW_EINVAL, "out is NULL");
-  // physical u, v, h, zeta in FP64: zeta via a spectral curl in FP64
+// Physical FP64 u, v, h, zeta of the current state in out64 slots 0..3
+// (zeta by a spectral curl in FP64), on the handle's stream.
+static int phys_uvhz(sw_handle* h) {
   OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, 1.0}};
   int rc = phys_outputs(h, os, 3);
   if (rc) return rc;
@@ -1012,6 +1010,41 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   ri.ob[0] = -1;
   ri.sa[0] = 1.0;
   CK(h, launch_row_inv<double, double>(ri, h->stream));
+  return SW_OK;
+}
+
+namespace lm {
+// hooks for the semi-Lagrangian interval (gbla.cu)
+int handle_info(sw_handle* h, HandleInfo* hi) {
+  if (!h || !hi) return SW_EINVAL;
+  hi->N = h->g.N;
+  hi->dt = h->p.dt;
+  hi->f0 = h->p.f0;
+  hi->adv_x = h->p.adv_x;
+  hi->adv_y = h->p.adv_y;
+  hi->model = h->p.model;
+  hi->lm_open = h->lm_open;
+  hi->stream = h->stream;
+  return SW_OK;
+}
+int handle_phys_uvhz(sw_handle* h, const double** out) {
+  const int rc = phys_uvhz(h);
+  if (rc) return rc;
+  *out = h->out64;
+  return SW_OK;
+}
+void handle_set_error(sw_handle* h, const std::string& msg) {
+  if (h) h->err = msg;
+}
+}  // namespace lm
+
+extern "C" int sw_diag(sw_handle* h, double out[3]) {
+  if (!h) return SW_EINVAL;
+  h->err.clear();
+  if (!out) return fail(h, SW_EINVAL, "out is NULL");
+  int rc = phys_uvhz(h);
+  if (rc) return rc;
+  const Geom& g = h->g;
   CK(h, launch_diag(h->out64, g.np, h->p.f0, h->p.c2, h->part, h->diag_blocks, h->dres, h->stream));
   h->launches += 5;
   double res[4] = {0, 0, 0, 0};

@@ -1,7 +1,11 @@
 // launch.cuh -- host-side launchers for the kernels of kernels.cuh and
 // stage.cuh.  Instantiated once per precision (kernels_f32.cu, kernels_f64.cu).
 #pragma once
+#include <string>
+
 #include "stage.cuh"
+
+struct sw_handle;
 
 namespace lm {
 
@@ -58,6 +62,19 @@ cudaError_t launch_diag(const double* phys, long long np, double f0, double c2, 
                         double* out, cudaStream_t s);
 cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s);
 cudaError_t launch_spectrum_shells(const double2* F, int K, int KXP, double* acc, cudaStream_t s);
+
+// Handle hooks for other translation units (defined in lagmean.cu).
+struct HandleInfo {
+  int N, model;
+  double dt, f0, adv_x, adv_y;
+  bool lm_open;
+  cudaStream_t stream;
+};
+int handle_info(sw_handle* h, HandleInfo* hi);
+// FP64 physical u, v, h, zeta of the state (4 * N * N doubles in the handle's
+// staging buffer, valid until the handle's next call), on its stream
+int handle_phys_uvhz(sw_handle* h, const double** out);
+void handle_set_error(sw_handle* h, const std::string& msg);
 
 #ifdef LM_INSTANTIATE
 // Raise the dynamic shared-memory limit of every kernel once (outside any

@@ -46,7 +46,8 @@ def test_struct_layout_matches_c(tmp_path, lm):
                     "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(sw_params),"
                     " sizeof(lm_params), sizeof(lm_result), offsetof(sw_params, dt),"
                     " offsetof(lm_result, on_device), sizeof(sw_server_params), sizeof(sw_job),"
-                    " offsetof(sw_job, tag), sizeof(sw_job_done), sizeof(sw_server_stats)); return 0;}\n")
+                    " offsetof(sw_job, tag), sizeof(sw_job_done), sizeof(sw_server_stats));"
+                    " printf(\"%zu %zu\\n\", sizeof(sl_params), offsetof(sl_params, n_steps)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
@@ -54,7 +55,8 @@ def test_struct_layout_matches_c(tmp_path, lm):
     assert got == [C.sizeof(api.sw_params), C.sizeof(api.lm_params), C.sizeof(api.lm_result),
                    api.sw_params.dt.offset, api.lm_result.on_device.offset,
                    C.sizeof(api.sw_server_params), C.sizeof(api.sw_job), api.sw_job.tag.offset,
-                   C.sizeof(api.sw_job_done), C.sizeof(api.sw_server_stats)]
+                   C.sizeof(api.sw_job_done), C.sizeof(api.sw_server_stats),
+                   C.sizeof(api.sl_params), api.sl_params.n_steps.offset]
 
 
 @pytest.mark.parametrize("field,value", [("N", 48), ("N", 8), ("N", 4096), ("dt", 0.0), ("dt", -1.0),
@@ -154,3 +156,14 @@ def test_spectrum_rejects_null_handle(lm):
     lib = lm.api.load()
     out = np.zeros(4)
     assert lib.sw_spectrum(None, None, 0, out.ctypes.data_as(lm.api._DP), 4) == lm.api.SW_EINVAL
+
+
+def test_sl_arguments_rejected_before_device_use(lm):
+    lib = lm.api.load()
+    s = C.c_void_p()
+    p = lm.make_sl_params(n_steps=4)
+    assert lib.sw_sl_create(None, C.byref(p), C.byref(s)) == lm.api.SW_EINVAL
+    assert "sw_sl" in lm.sw_last_error(None)
+    assert lib.sw_sl_step(None, 1) == lm.api.SW_EINVAL
+    assert lib.sw_sl_end(None, None) == lm.api.SW_EINVAL
+    lib.sw_sl_destroy(None)  # no-op
