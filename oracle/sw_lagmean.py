@@ -34,7 +34,9 @@ What is computed (one averaging interval [tau, tau+T], Sec. 2, Eq. (ave)):
   w takes its limit u/2 (the partial mean position is x + u s/2 + O(s^2));
 * Eulerian means, Eq. (ave): E = int f dt, mean E/T;
 * time stepping: classical RK4 with a diagonal integrating factor
-  exp(-nu |k|^8 t) (the paper's forward Euler and Heun steppers are not used);
+  exp(-nu |k|^8 t); optionally the paper's own steppers, Heun (Sec. 4.1) and
+  forward Euler (Sec. 4.2.1), with the same integrating factor, and the
+  paper's Laplacian viscosity (-nu |k|^2) in place of the hyperviscosity;
   the Lagrangian-mean fields share the RK stages with the dynamics (on-the-fly
   computation, Sec. 5).
 
@@ -64,7 +66,7 @@ class SWOracle:
     _stage_hook = None  # test hook: called with each RK stage state
 
     def __init__(self, N, dt, u, v, h, f0=1.0, c2=1.0, nu8=0.0, lm_nu8=None,
-                 model="sw", adv=(0.0, 0.0)):
+                 model="sw", adv=(0.0, 0.0), stepper="rk4", visc="hyper8"):
         if N % 2 or N < 8:
             raise ValueError("N must be even and >= 8")
         self.N = int(N)
@@ -77,6 +79,12 @@ class SWOracle:
             raise ValueError(model)
         self.model = model
         self.adv = (float(adv[0]), float(adv[1]))
+        if stepper not in ("rk4", "heun", "euler") or visc not in ("hyper8", "laplace"):
+            raise ValueError((stepper, visc))
+        self.stepper = stepper
+        # nu8 is the coefficient of the viscous term -nu8 |k|^(2p): p = 4
+        # (hyperviscosity) or p = 1 (the paper's Laplacian, Eq. sw_momentum_dimless)
+        self.visc_p = 4 if visc == "hyper8" else 1
         N = self.N
         self.K = (N - 1) // 3
         self.kx = np.arange(N // 2 + 1, dtype=np.float64)[None, :]
@@ -242,8 +250,8 @@ class SWOracle:
         return st
 
     def _factors(self):
-        """Half-step integrating factors exp(L dt/2), L = -nu |k|^8."""
-        k8 = self.k2 ** 4
+        """Half-step integrating factors exp(L dt/2), L = -nu |k|^(2p)."""
+        k8 = self.k2 ** self.visc_p
         e_sw = np.exp(-self.nu8 * k8 * self.dt * 0.5)
         e_lm = np.exp(-self.lm_nu8 * k8 * self.dt * 0.5)
         return {"sw": e_sw, "G": e_lm, "P": e_lm, "E": np.ones_like(k8)}
@@ -260,6 +268,42 @@ class SWOracle:
 
     def _efac_tree(self, st, fac):
         return {k: self._map(lambda _x, f=fac[k]: f, v) for k, v in st.items()}
+
+    def _step(self, s0):
+        {"rk4": self._rk4_step, "heun": self._heun_step, "euler": self._euler_step}[self.stepper](s0)
+
+    def _heun_step(self, s0):
+        """Heun's method (the paper's stepper in Sec. 4.1) with the integrating
+        factor: a = N(y_n), y1 = E^2 (y_n + dt a), b = N(y1, t + dt),
+        y_{n+1} = E^2 y_n + dt/2 (E^2 a + b)."""
+        dt = self.dt
+        y = self._state()
+        E = self._efac_tree(y, self._factors())
+        m = self._map
+        a = self._rhs(y, s0)
+        y1 = m(lambda yy, aa, e: e * e * (yy + dt * aa), y, a, E)
+        b = self._rhs(y1, s0 + dt)
+        yn = m(lambda yy, aa, bb, e: e * e * yy + (dt / 2.0) * (e * e * aa + bb), y, a, b, E)
+        self._commit(yn)
+
+    def _euler_step(self, s0):
+        """Forward Euler (the paper's stepper in Sec. 4.2.1) with the
+        integrating factor: y_{n+1} = E^2 (y_n + dt N(y_n))."""
+        dt = self.dt
+        y = self._state()
+        E = self._efac_tree(y, self._factors())
+        a = self._rhs(y, s0)
+        self._commit(self._map(lambda yy, aa, e: e * e * (yy + dt * aa), y, a, E))
+
+    def _commit(self, yn):
+        self.uh, self.vh, self.hh = yn["sw"]
+        if self.lm is not None:
+            self.lm["G"] = yn["G"]
+            if "P" in yn:
+                self.lm["P"] = yn["P"]
+            if "E" in yn:
+                self.lm["E"] = yn["E"]
+        self.t += self.dt
 
     def _rk4_step(self, s0):
         dt = self.dt
@@ -290,7 +334,7 @@ class SWOracle:
         if self.lm is not None:
             raise RuntimeError("an averaging interval is open")
         for _ in range(int(nsteps)):
-            self._rk4_step(0.0)
+            self._step(0.0)
 
     def lmean_step(self, nsteps):
         lm = self.lm
@@ -300,7 +344,7 @@ class SWOracle:
             raise ValueError("more steps than remain in the interval")
         for _ in range(int(nsteps)):
             # s = t - tau counted in whole steps (never accumulated).
-            self._rk4_step(lm["done"] * self.dt)
+            self._step(lm["done"] * self.dt)
             lm["done"] += 1
 
     def lmean_end(self):

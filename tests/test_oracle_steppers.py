@@ -1,0 +1,72 @@
+"""Pins of the oracle's alternative steppers and viscosity (the paper's own
+setup: Heun, Sec. 4.1; forward Euler and the Laplacian viscosity, Sec. 4.2.1).
+
+No GPU.  For a uniform flow only the Coriolis term acts, so u + i v is
+multiplied each step by the stepper's stability polynomial R(-i f0 dt); with
+a Laplacian on a single small mode the integrating factor makes the damping
+exact, z_n = (exp(-nu |k|^2 dt) R(-i f0 dt))^n z_0; on a nonlinear flow with
+an open Strategy-1 interval (whose right-hand sides depend on the stage time
+through s u) the error against a fine RK4 reference falls at the stepper's
+order under dt halving.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import sw_inputs as si
+from oracle import SWOracle, rel_l2
+
+R = {"euler": lambda z: 1 + z, "heun": lambda z: 1 + z + z * z / 2,
+     "rk4": lambda z: 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24}
+
+
+@pytest.mark.parametrize("stepper", ["euler", "heun"])
+def test_uniform_inertial_oscillation(stepper):
+    N, dt, f0, U0, n = 16, 5e-3, 1.3, 0.7, 300
+    u, v, h = si.uniform_flow(N, U0, 0.0)
+    o = SWOracle(N, dt, u, v, h, f0=f0, stepper=stepper)
+    o.lmean_begin(1, fields=("u", "v"), pos=True, eulerian=True, n_steps=n)
+    o.lmean_step(n)
+    z = U0 * R[stepper](-1j * f0 * dt) ** n
+    uu, vv, _ = o.fields()
+    assert abs(uu.mean() - z.real) < 1e-13 and abs(vv.mean() - z.imag) < 1e-13
+    assert np.abs(uu - uu.mean()).max() < 1e-14
+
+
+@pytest.mark.parametrize("stepper", ["euler", "heun", "rk4"])
+def test_laplacian_integrating_factor_exact(stepper):
+    N, dt, f0, n = 16, 1e-2, 1.3, 120
+    kx, ky = 2, 1
+    nu = 0.2 / (kx * kx + ky * ky)
+    x = 2 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    eps = 1e-9
+    u = eps * np.cos(kx * X + ky * Y)
+    v = eps * 0.3 * np.sin(kx * X + ky * Y)
+    o = SWOracle(N, dt, u, v, 1.0 + 0 * u, f0=f0, c2=0.0, nu8=nu, stepper=stepper, visc="laplace")
+    z0 = o.uh[ky, kx] + 1j * o.vh[ky, kx]
+    o.step(n)
+    z1 = o.uh[ky, kx] + 1j * o.vh[ky, kx]
+    amp = math.exp(-nu * (kx * kx + ky * ky) * dt) * R[stepper](-1j * f0 * dt)
+    assert abs(z1 - z0 * amp ** n) < 1e-6 * abs(z0)
+
+
+def _run(stepper, dt, T=0.4, N=32):
+    u, v, h = si.smooth_flow(N, 2, seed=8, uamp=0.15, eamp=0.05)
+    n = int(round(T / dt))
+    o = SWOracle(N, dt, u, v, h, nu8=0.0, stepper=stepper)
+    o.lmean_begin(1, fields=("zeta",), pos=True, eulerian=False, n_steps=n)
+    o.lmean_step(n)
+    return o.lmean_end()
+
+
+@pytest.mark.parametrize("stepper,order", [("euler", 1), ("heun", 2)])
+def test_order_of_accuracy_with_an_open_interval(stepper, order):
+    ref = _run("rk4", 1e-3 / 4)
+    errs = []
+    for dt in (4e-3, 2e-3):
+        out = _run(stepper, dt)
+        errs.append(max(rel_l2(out["zeta"], ref["zeta"]), np.abs(out["pos_x"] - ref["pos_x"]).max()))
+    ratio = errs[0] / errs[1]
+    assert 2 ** order * 0.8 < ratio < 2 ** order * 1.25, (errs, ratio)
