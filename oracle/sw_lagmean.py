@@ -36,7 +36,8 @@ What is computed (one averaging interval [tau, tau+T], Sec. 2, Eq. (ave)):
 * time stepping: classical RK4 with a diagonal integrating factor
   exp(-nu |k|^8 t); optionally the paper's own steppers, Heun (Sec. 4.1) and
   forward Euler (Sec. 4.2.1), with the same integrating factor, and the
-  paper's Laplacian viscosity (-nu |k|^2) in place of the hyperviscosity;
+  paper's Laplacian viscosity (-nu |k|^2 on u and v only, as in Eq.
+  sw_momentum_dimless) in place of the hyperviscosity;
   the Lagrangian-mean fields share the RK stages with the dynamics (on-the-fly
   computation, Sec. 5).
 
@@ -250,11 +251,15 @@ class SWOracle:
         return st
 
     def _factors(self):
-        """Half-step integrating factors exp(L dt/2), L = -nu |k|^(2p)."""
+        """Half-step integrating factors exp(L dt/2), L = -nu |k|^(2p), per
+        field of (u, v, h): the Laplacian of Eq. (sw_momentum_dimless) acts on
+        the momentum only (the mass equation, Eq. sw_mass_dimless, has no
+        viscous term); the hyperviscosity acts on u, v and h."""
         k8 = self.k2 ** self.visc_p
         e_sw = np.exp(-self.nu8 * k8 * self.dt * 0.5)
+        e_h = np.ones_like(k8) if self.visc_p == 1 else e_sw
         e_lm = np.exp(-self.lm_nu8 * k8 * self.dt * 0.5)
-        return {"sw": e_sw, "G": e_lm, "P": e_lm, "E": np.ones_like(k8)}
+        return {"sw": (e_sw, e_sw, e_h), "G": e_lm, "P": e_lm, "E": np.ones_like(k8)}
 
     @staticmethod
     def _map(fn, *trees):
@@ -267,7 +272,10 @@ class SWOracle:
         return fn(*trees)
 
     def _efac_tree(self, st, fac):
-        return {k: self._map(lambda _x, f=fac[k]: f, v) for k, v in st.items()}
+        """Factor tree matching the state: a tuple of factors is per field, a
+        single factor applies to every field of its group."""
+        return {k: (fac[k] if isinstance(fac[k], tuple) else self._map(lambda _x, f=fac[k]: f, v))
+                for k, v in st.items()}
 
     def _step(self, s0):
         {"rk4": self._rk4_step, "heun": self._heun_step, "euler": self._euler_step}[self.stepper](s0)

@@ -70,3 +70,23 @@ def test_order_of_accuracy_with_an_open_interval(stepper, order):
         errs.append(max(rel_l2(out["zeta"], ref["zeta"]), np.abs(out["pos_x"] - ref["pos_x"]).max()))
     ratio = errs[0] / errs[1]
     assert 2 ** order * 0.8 < ratio < 2 ** order * 1.25, (errs, ratio)
+
+
+@pytest.mark.parametrize("visc", ["laplace", "hyper8"])
+def test_viscosity_placement_on_depth(visc):
+    # at rest with c2 = 0 the depth perturbation has no dynamics: the
+    # Laplacian of Eq. (sw_momentum_dimless) leaves it unchanged (the mass
+    # equation has no viscous term); the hyperviscosity damps each mode by
+    # exp(-nu |k|^8 t)
+    N, dt, n, nu = 16, 1e-2, 50, 3e-4
+    x = 2 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    kx, ky = 3, 2
+    h = 1.0 + 0.1 * np.cos(kx * X + ky * Y)
+    o = SWOracle(N, dt, 0 * X, 0 * X, h, f0=0.7, c2=0.0, nu8=nu, stepper="heun", visc=visc)
+    e0 = o.hh[ky, kx]
+    o.step(n)
+    k2 = kx * kx + ky * ky
+    damp = 1.0 if visc == "laplace" else math.exp(-nu * k2 ** 4 * dt * n)
+    assert abs(o.hh[ky, kx] - e0 * damp) < 1e-14
+    assert np.abs(o.uh).max() < 1e-300 and np.abs(o.vh).max() < 1e-300
