@@ -76,18 +76,38 @@ extern "C" {
 typedef struct sw_handle sw_handle;
 
 /* Model and discretisation parameters (sw_create). */
+/* Time steppers, all with the diagonal integrating factor exp(-nu |k|^2p dt)
+ * of the viscous term:
+ *   SW_STEP_RK4    classical four-stage Runge-Kutta (the default);
+ *   SW_STEP_HEUN   Heun's method, the paper's stepper in Sec. 4.1:
+ *                  y1 = E^2 (y + dt a), y' = E^2 y + dt/2 (E^2 a + b);
+ *   SW_STEP_EULER  forward Euler, the paper's stepper in Sec. 4.2.1:
+ *                  y' = E^2 (y + dt a);
+ * (a, b: right-hand sides at the stages, E = exp(-nu |k|^2p dt/2)).  The
+ * Lagrangian-mean fields share the stages with the dynamics.
+ * Viscosity: SW_VISC_HYPER8 -nu |k|^8 (the default), SW_VISC_LAPLACE
+ * -nu |k|^2 (the paper's Laplacian, Eq. (sw_momentum_dimless)), with
+ * nu = nu8 on u, v, h and lm_nu8 on the Lagrangian-mean fields. */
+#define SW_STEP_RK4 0
+#define SW_STEP_HEUN 1
+#define SW_STEP_EULER 2
+#define SW_VISC_HYPER8 0
+#define SW_VISC_LAPLACE 1
+
 typedef struct sw_params {
   int32_t N;         /* grid points per side: power of two, 16..2048        */
   int32_t precision; /* SW_PREC_FP64 or SW_PREC_FP32                        */
   int32_t model;     /* SW_MODEL_SW or SW_MODEL_KINEMATIC                    */
-  int32_t reserved;  /* must be 0                                           */
-  double dt;         /* RK4 time step, > 0                                  */
+  int32_t stepper;   /* SW_STEP_RK4 (0), SW_STEP_HEUN or SW_STEP_EULER       */
+  double dt;         /* time step, > 0                                      */
   double f0;         /* Coriolis parameter (1/Ro)                           */
   double c2;         /* squared gravity-wave speed g H (1/Fr^2), >= 0        */
-  double nu8;        /* hyperviscosity on u, v, h: -nu8 |k|^8, >= 0          */
-  double lm_nu8;     /* hyperviscosity on the Lagrangian-mean fields, >= 0   */
+  double nu8;        /* viscosity coefficient on u, v, h (see visc), >= 0    */
+  double lm_nu8;     /* viscosity coefficient on the Lagrangian-mean fields  */
   double adv_x;      /* advection velocity of SW_MODEL_KINEMATIC            */
   double adv_y;
+  int32_t visc;      /* SW_VISC_HYPER8 (0) or SW_VISC_LAPLACE               */
+  int32_t reserved;  /* must be 0                                           */
 } sw_params;
 
 /* One averaging interval (lmean_begin). */

@@ -37,9 +37,10 @@ SW_K_COUNT = 8
 
 class sw_params(C.Structure):
     _fields_ = [("N", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32),
-                ("reserved", C.c_int32), ("dt", C.c_double), ("f0", C.c_double),
+                ("stepper", C.c_int32), ("dt", C.c_double), ("f0", C.c_double),
                 ("c2", C.c_double), ("nu8", C.c_double), ("lm_nu8", C.c_double),
-                ("adv_x", C.c_double), ("adv_y", C.c_double)]
+                ("adv_x", C.c_double), ("adv_y", C.c_double), ("visc", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class lm_params(C.Structure):
@@ -176,11 +177,13 @@ def _ptr(a):
 
 
 def make_params(N, dt, precision="f64", model="sw", f0=1.0, c2=1.0, nu8=0.0, lm_nu8=None,
-                adv=(0.0, 0.0)) -> sw_params:
+                adv=(0.0, 0.0), stepper="rk4", visc="hyper8") -> sw_params:
     p = sw_params()
     p.N = int(N)
     p.precision = {"f64": SW_PREC_FP64, "f32": SW_PREC_FP32}[precision]
     p.model = {"sw": SW_MODEL_SW, "kinematic": SW_MODEL_KINEMATIC}[model]
+    p.stepper = {"rk4": 0, "heun": 1, "euler": 2}[stepper]
+    p.visc = {"hyper8": 0, "laplace": 1}[visc]
     p.reserved = 0
     p.dt, p.f0, p.c2, p.nu8 = float(dt), float(f0), float(c2), float(nu8)
     p.lm_nu8 = float(nu8 if lm_nu8 is None else lm_nu8)

@@ -130,6 +130,11 @@ struct Layout {
 
 struct StepConsts {
   double dt, f0, c2, adv_x, adv_y;
+  int stepper;  // SW_STEP_* (0 RK4, 1 Heun, 2 forward Euler)
+  int pad;
 };
+
+// stages per step of a stepper
+__host__ __device__ __forceinline__ int stage_count(int stepper) { return stepper == 0 ? 4 : (stepper == 1 ? 2 : 1); }
 
 }  // namespace lm

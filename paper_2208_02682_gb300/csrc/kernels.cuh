@@ -333,8 +333,9 @@ __global__ void __launch_bounds__(256) k_row_fwd(const __grid_constant__ RowFwdA
 // ---------------------------------------------------------------------------
 // Interval time of a stage: s = (steps done + c_stage) * dt, from the device
 // step counter (never accumulated).
-__device__ __forceinline__ double stage_time(const long long* ctr, int stage, double dt) {
-  const double c = stage == 0 ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+// time of a stage in steps: RK4 (0, 1/2, 1/2, 1), Heun (0, 1), Euler (0)
+__device__ __forceinline__ double stage_time(const long long* ctr, int stage, double dt, int stepper) {
+  const double c = stage == 0 ? 0.0 : (stepper != 0 || stage == 3 ? 1.0 : 0.5);
   return ((double)(*ctr) + c) * dt;
 }
 

@@ -78,11 +78,11 @@ static int fail_cuda(sw_handle* h, const char* what, cudaError_t e) {
 
 // ---------------------------------------------------------------------------
 // Field layout of a configuration.
-static Layout build_layout(int model, int strategy, int fields, int eulerian) {
+static Layout build_layout(const sw_params& p, int strategy, int fields, int eulerian) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   L.strategy = strategy;
-  L.model = model;
+  L.model = p.model;
   L.p_zv = L.p_zu = L.p_ke = L.p_hu = L.p_hv = L.p_q = -1;
   for (int j = 0; j < NLMF; ++j) L.f_g[j] = L.f_e[j] = L.p_g[j] = -1;
   L.f_p[0] = L.f_p[1] = L.p_p[0] = L.p_p[1] = L.i_xi[0] = L.i_xi[1] = -1;
@@ -91,7 +91,9 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
   L.f_v = nf++;
   L.f_h = nf++;
   for (int f = 0; f < 3; ++f) {
-    L.fclass[f] = IF_DYN;
+    // the Laplacian acts on momentum only (Eq. sw_momentum_dimless; the mass
+    // equation has no viscous term), the hyperviscosity on u, v and h
+    L.fclass[f] = (f == 2 && p.visc == SW_VISC_LAPLACE) ? IF_NONE : IF_DYN;
     L.fkahan[f] = 0;
     L.frole[f] = R_U + f;
     L.fslot[f] = 0;
@@ -138,7 +140,7 @@ static Layout build_layout(int model, int strategy, int fields, int eulerian) {
     L.pc[np] = c;
     return np++;
   };
-  if (model == SW_MODEL_SW) {
+  if (p.model == SW_MODEL_SW) {
     L.p_zv = addp(PK_ZV, -1, -1, 0);
     L.p_zu = addp(PK_ZU, -1, -1, 0);
     L.p_ke = addp(PK_KE, -1, -1, 0);
@@ -256,6 +258,7 @@ struct BatchExec {
   int64_t kernels_per_step = 0;
   int64_t launches = 0;
   bool built = false;
+  int nstages = 4;  // stages per step of the members' (common) stepper
   std::string err;
 };
 
@@ -279,7 +282,7 @@ static void fill_desc(sw_handle* h, RunDesc<T>& d, int ppb) {
   const Geom& g = h->g;
   d.g = g;
   d.L = h->L;
-  d.c = StepConsts{h->p.dt, h->p.f0, h->p.c2, h->p.adv_x, h->p.adv_y};
+  d.c = StepConsts{h->p.dt, h->p.f0, h->p.c2, h->p.adv_x, h->p.adv_y, h->p.stepper, 0};
   d.y = (cplx<T>*)h->y;
   d.ysa = (cplx<T>*)h->ys;
   d.ysb = (cplx<T>*)h->ys2;
@@ -321,6 +324,12 @@ static int batch_build_t(BatchExec* b) {
   }
   b->start.assign((size_t)KT_COUNT * (n + 1), 0);
   const size_t cs = sizeof(cplx<T>);
+  for (int r = 1; r < n; ++r)
+    if (b->members[r]->p.stepper != b->members[0]->p.stepper) {
+      b->err = "batch members need the same stepper";
+      return SW_EINVAL;
+    }
+  b->nstages = n > 0 ? stage_count(b->members[0]->p.stepper) : 4;
   // row-pass groups per row: the largest number every member allows (the
   // batch's row-pass blocks all have Bp * Wp * N/8 threads)
   int W = 1 << 20;
@@ -421,7 +430,7 @@ static cudaError_t enqueue_batch_step(BatchExec* b, cudaStream_t s, Prof* pf, in
   const int n = b->nruns;
   cudaError_t e;
   static const int order[KT_COUNT] = {KT_COL_INV, KT_ROW_INV, KT_PHYS_Q, KT_ROW_PROD, KT_COL_FWD, KT_UPDATE};
-  for (int stage = 0; stage < 4; ++stage) {
+  for (int stage = 0; stage < b->nstages; ++stage) {
     for (int oi = 0; oi < KT_COUNT; ++oi) {
       const int k = order[oi];
       const int total = b->start[(size_t)k * (n + 1) + n];
@@ -633,6 +642,8 @@ static int validate(const sw_params* p, std::string& why) {
   if (p->precision != SW_PREC_FP64 && p->precision != SW_PREC_FP32) { why = "precision must be SW_PREC_FP64 or SW_PREC_FP32"; return SW_EINVAL; }
   if (p->model != SW_MODEL_SW && p->model != SW_MODEL_KINEMATIC) { why = "model must be SW_MODEL_SW or SW_MODEL_KINEMATIC"; return SW_EINVAL; }
   if (p->reserved != 0) { why = "reserved must be 0"; return SW_EINVAL; }
+  if (p->stepper < SW_STEP_RK4 || p->stepper > SW_STEP_EULER) { why = "stepper must be SW_STEP_RK4, SW_STEP_HEUN or SW_STEP_EULER"; return SW_EINVAL; }
+  if (p->visc != SW_VISC_HYPER8 && p->visc != SW_VISC_LAPLACE) { why = "visc must be SW_VISC_HYPER8 or SW_VISC_LAPLACE"; return SW_EINVAL; }
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { why = "dt must be finite and > 0"; return SW_EINVAL; }
   if (!std::isfinite(p->f0) || !std::isfinite(p->adv_x) || !std::isfinite(p->adv_y)) { why = "f0 and adv must be finite"; return SW_EINVAL; }
   if (!(p->c2 >= 0.0) || !std::isfinite(p->c2)) { why = "c2 must be finite and >= 0"; return SW_EINVAL; }
@@ -710,7 +721,7 @@ static void host_tables(const sw_params& p, const Geom& g, void* ef_host, void* 
     for (int kx = 0; kx < g.KXP; ++kx) {
       const double ky = kyi - g.K;
       const double k2 = (double)kx * kx + ky * ky;
-      const double k8 = k2 * k2 * k2 * k2;
+      const double k8 = p.visc == SW_VISC_LAPLACE ? k2 : k2 * k2 * k2 * k2;  // |k|^2p
       const long long m = (long long)kyi * g.KXP + kx;
       ef[m] = (T)std::exp(-p.nu8 * k8 * p.dt * 0.5);
       ef[g.ms + m] = (T)std::exp(-p.lm_nu8 * k8 * p.dt * 0.5);
@@ -799,7 +810,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
     delete h;
     return fail(nullptr, SW_ECUDA, m);
   }
-  h->L = build_layout(p->model, 0, 0, 0);
+  h->L = build_layout(*p, 0, 0, 0);
   h->self = new (std::nothrow) BatchExec();
   if (!h->self) {
     cudaFree(h->arena);
@@ -854,7 +865,7 @@ extern "C" int lmean_begin(sw_handle* h, const lm_params* lp) {
   const int scal = lp->fields & (LM_ZETA | LM_H | LM_U | LM_V | LM_Q);
   if (!scal && !(lp->fields & LM_POS)) return fail(h, SW_EINVAL, "no field selected");
   if (!scal && lp->eulerian) return fail(h, SW_EINVAL, "Eulerian means need a scalar field");
-  Layout L = build_layout(h->p.model, lp->strategy, lp->fields, lp->eulerian);
+  Layout L = build_layout(h->p, lp->strategy, lp->fields, lp->eulerian);
   const Geom& g = h->g;
   const size_t cs = 2 * h->tsz;
   // zero the mean fields, their compensation terms and the step counter
@@ -941,7 +952,7 @@ extern "C" int lmean_end(sw_handle* h, const lm_result* out) {
     if ((rc = copy_out(h, dst[i], i, out->on_device))) return rc;
   if (!out->on_device) CK(h, cudaStreamSynchronize(h->stream));
   h->lm_open = false;
-  set_layout(h, build_layout(h->p.model, 0, 0, 0));
+  set_layout(h, build_layout(h->p, 0, 0, 0));
   return SW_OK;
 }
 
@@ -1068,6 +1079,7 @@ struct BlobHeader {
   char magic[8];
   int32_t version, N, precision, model;
   double dt, f0, c2, nu8, lm_nu8, adv_x, adv_y;
+  int32_t stepper, visc;
   int32_t lm_open, nf;
   lm_params lp;
   int64_t done, steps_total;
@@ -1095,6 +1107,7 @@ extern "C" int sw_get_state(sw_handle* h, void* blob, size_t* size) {
   hd.N = h->p.N; hd.precision = h->p.precision; hd.model = h->p.model;
   hd.dt = h->p.dt; hd.f0 = h->p.f0; hd.c2 = h->p.c2; hd.nu8 = h->p.nu8; hd.lm_nu8 = h->p.lm_nu8;
   hd.adv_x = h->p.adv_x; hd.adv_y = h->p.adv_y;
+  hd.stepper = h->p.stepper; hd.visc = h->p.visc;
   hd.lm_open = h->lm_open ? 1 : 0;
   hd.nf = nf;
   hd.lp = h->lp;
@@ -1119,10 +1132,10 @@ extern "C" int sw_set_state(sw_handle* h, const void* blob, size_t size) {
   if (std::memcmp(hd.magic, "LAGMEAN1", 8) != 0 || hd.version != 1) return fail(h, SW_EINVAL, "not a state blob");
   if (hd.N != h->p.N || hd.precision != h->p.precision || hd.model != h->p.model || hd.dt != h->p.dt ||
       hd.f0 != h->p.f0 || hd.c2 != h->p.c2 || hd.nu8 != h->p.nu8 || hd.lm_nu8 != h->p.lm_nu8 ||
-      hd.adv_x != h->p.adv_x || hd.adv_y != h->p.adv_y)
+      hd.adv_x != h->p.adv_x || hd.adv_y != h->p.adv_y || hd.stepper != h->p.stepper || hd.visc != h->p.visc)
     return fail(h, SW_EINVAL, "blob parameters differ from the handle's");
-  Layout L = hd.lm_open ? build_layout(h->p.model, hd.lp.strategy, hd.lp.fields, hd.lp.eulerian)
-                        : build_layout(h->p.model, 0, 0, 0);
+  Layout L = hd.lm_open ? build_layout(h->p, hd.lp.strategy, hd.lp.fields, hd.lp.eulerian)
+                        : build_layout(h->p, 0, 0, 0);
   if (L.nf != hd.nf || size < blob_size(h, hd.nf)) return fail(h, SW_EINVAL, "blob size mismatch");
   const size_t fb = (size_t)hd.nf * h->g.ms * 2 * h->tsz;
   const char* src = (const char*)blob + sizeof(hd);

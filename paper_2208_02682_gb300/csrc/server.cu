@@ -4,7 +4,8 @@
 // arrival order while the job-state bytes (sw_state_bytes) fit in the budget
 // and a slot is free, creating the job's handle from its initial condition
 // and opening its interval; (2) groups the active jobs by compatible block
-// shapes (all grids 64..512 together, every other size on its own) and
+// shapes and stepper (all grids 64..512 together, every other size on its
+// own; one stepper per group) and
 // advances each group as one sw_batch by the largest step count no member
 // overshoots (at most chunk_steps); (3) completes the jobs whose interval has
 // ended: lmean_end into the caller's host buffers, handle released.
@@ -41,7 +42,9 @@ struct Group {
   sw_batch* batch = nullptr;
 };
 
-int group_key(int N) { return (N >= 64 && N <= 512) ? 0 : N; }
+// batch group of a job: sizes 64..512 share one group; every stepper has its
+// own groups (a batch runs one stepper)
+int group_key(const sw_params& p) { return ((p.N >= 64 && p.N <= 512) ? 0 : p.N) * 4 + p.stepper; }
 
 }  // namespace
 
@@ -128,7 +131,7 @@ struct sw_server {
   // (re)build the batch groups when membership changed
   int regroup() {
     std::map<int, std::vector<sw_handle*>> want;
-    for (auto& jb : active) want[group_key(jb.j.params.N)].push_back(jb.h);
+    for (auto& jb : active) want[group_key(jb.j.params)].push_back(jb.h);
     bool same = want.size() == groups.size();
     if (same)
       for (auto& kv : want) {
@@ -166,11 +169,11 @@ struct sw_server {
     for (auto& kv : groups) {
       int64_t k = p.chunk_steps;
       for (auto& jb : active)
-        if (group_key(jb.j.params.N) == kv.first) k = std::min(k, jb.remaining);
+        if (group_key(jb.j.params) == kv.first) k = std::min(k, jb.remaining);
       if (k <= 0) continue;
       int rc = sw_batch_step(kv.second.batch, k);
       for (auto& jb : active)
-        if (group_key(jb.j.params.N) == kv.first) jb.remaining = rc == SW_OK ? jb.remaining - k : -1;
+        if (group_key(jb.j.params) == kv.first) jb.remaining = rc == SW_OK ? jb.remaining - k : -1;
     }
     {
       std::lock_guard<std::mutex> lk(mu);

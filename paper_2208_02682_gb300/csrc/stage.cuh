@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const bool kin = L.model == 1;
   const T adv_x = (T)d.c.adv_x, adv_y = (T)d.c.adv_y;
   const T f0 = (T)d.c.f0;
-  const double s = stage_time(d.ctr, stage, d.c.dt);
+  const double s = stage_time(d.ctr, stage, d.c.dt, d.c.stepper);
   const bool s0 = !(s > 0.0);
   const T inv_s = s0 ? (T)0 : (T)(1.0 / s);
   const T inv_dx = (T)((double)N / 6.283185307179586476925286766559);
@@ -411,7 +411,8 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
 //   stage 1: b = N(y1)       acc += 2 E b           y2 = E y_n + dt/2 b
 //   stage 2: c = N(y2)       acc += 2 E c           y3 = E^2 y_n + dt E c
 //   stage 3: d = N(y3)       y_{n+1} = E^2 y_n + dt/6 (acc + d)
-// with E = exp(-nu |k|^8 dt/2).  Stage inputs alternate between two buffers
+// with E = exp(-nu |k|^2p dt/2) (Heun and forward Euler: see update_mode).
+// Stage inputs alternate between two buffers
 // (a thread reads other fields' stage inputs at its mode).
 __device__ __forceinline__ float kahan_add_rn(float sum, float add, float& comp) {
   const float yk = __fsub_rn(add, comp);
@@ -492,18 +493,27 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, doub
   const long long o = f * g.ms + m;
   const cplx<T> yn = d.y[o];
   cplx<T>* yout = stage == 1 ? d.ysb : d.ysa;
-  if (stage == 0) {
+  const int st = d.c.stepper;
+  const bool last = stage == stage_count(st) - 1;
+  if (!last && st != 0) {
+    // Heun, stage 0: acc = E^2 a, y1 = E^2 (y_n + dt a)
+    d.acc[o] = cscale<T>(rhs, E * E);
+    yout[o] = cscale<T>(cadd<T>(yn, cscale<T>(rhs, dt)), E * E);
+  } else if (stage == 0 && !last) {
     d.acc[o] = cscale<T>(rhs, E * E);
     yout[o] = cscale<T>(cadd<T>(yn, cscale<T>(rhs, (T)0.5 * dt)), E);
-  } else if (stage == 1) {
+  } else if (stage == 1 && !last) {
     d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
     yout[o] = cadd<T>(cscale<T>(yn, E), cscale<T>(rhs, (T)0.5 * dt));
   } else if (stage == 2) {
     d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
     yout[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(rhs, dt * E));
   } else {
-    const cplx<T> inc = cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)6);
+    // final stage: y_{n+1} = E^2 y_n + inc, with inc = dt/6 (acc + d) (RK4),
+    // dt/2 (acc + b) (Heun) or dt E^2 a (forward Euler)
     const T E2 = E * E;
+    const cplx<T> inc = st == 0 ? cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)6)
+                                : (st == 1 ? cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)2) : cscale<T>(rhs, dt * E2));
     if (d.comp && L.fkahan[f]) {
       cplx<T> cc = d.comp[o];
       cc.x *= E2;
@@ -530,14 +540,14 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
   const int mblocks = (int)((g.ms + 255) / 256);
   const int f = lb / mblocks;
   const long long m = (long long)(lb - f * mblocks) * 256 + threadIdx.x;
-  const double sd = stage_time(d.ctr, stage, d.c.dt);
+  const double sd = stage_time(d.ctr, stage, d.c.dt, d.c.stepper);
   if (m < g.ms) {
     const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
     if (kx <= g.K) {
       update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
     }
   }
-  if (stage == 3) {
+  if (stage == stage_count(d.c.stepper) - 1) {
     // the run's last block to finish advances its step counter (every block
     // of the run has read it above, before taking its ticket)
     __syncthreads();

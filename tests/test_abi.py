@@ -47,7 +47,8 @@ def test_struct_layout_matches_c(tmp_path, lm):
                     " sizeof(lm_params), sizeof(lm_result), offsetof(sw_params, dt),"
                     " offsetof(lm_result, on_device), sizeof(sw_server_params), sizeof(sw_job),"
                     " offsetof(sw_job, tag), sizeof(sw_job_done), sizeof(sw_server_stats));"
-                    " printf(\"%zu %zu\\n\", sizeof(sl_params), offsetof(sl_params, n_steps)); return 0;}\n")
+                    " printf(\"%zu %zu\\n\", sizeof(sl_params), offsetof(sl_params, n_steps));"
+                    " printf(\"%zu %zu\\n\", offsetof(sw_params, stepper), offsetof(sw_params, visc)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
@@ -56,12 +57,14 @@ def test_struct_layout_matches_c(tmp_path, lm):
                    api.sw_params.dt.offset, api.lm_result.on_device.offset,
                    C.sizeof(api.sw_server_params), C.sizeof(api.sw_job), api.sw_job.tag.offset,
                    C.sizeof(api.sw_job_done), C.sizeof(api.sw_server_stats),
-                   C.sizeof(api.sl_params), api.sl_params.n_steps.offset]
+                   C.sizeof(api.sl_params), api.sl_params.n_steps.offset,
+                   api.sw_params.stepper.offset, api.sw_params.visc.offset]
 
 
 @pytest.mark.parametrize("field,value", [("N", 48), ("N", 8), ("N", 4096), ("dt", 0.0), ("dt", -1.0),
                                          ("precision", 7), ("model", 3), ("nu8", -1.0),
-                                         ("c2", float("nan")), ("reserved", 1)])
+                                         ("c2", float("nan")), ("reserved", 1),
+                                         ("stepper", 3), ("stepper", -1), ("visc", 2)])
 def test_invalid_parameters_rejected_before_device_use(lm, field, value):
     p = lm.make_params(64, 1e-3)
     setattr(p, field, value)
