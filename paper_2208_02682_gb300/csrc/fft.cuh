@@ -188,8 +188,12 @@ __device__ void block_fft(cplx<T>* buf, int log2N, int bstride, const cplx<T>* _
 
 // Barrier over the group's G threads: the warp when G <= 32 (several groups
 // per warp execute the same instructions), else named barrier 1 + grp.
+// WARP: the caller guarantees G <= 32, so the kernel holds no named barrier
+// (a named barrier with a run-time id reserves all 16 of the block's
+// barriers, which limits the blocks resident on an SM).
+template <bool WARP = false>
 __device__ __forceinline__ void group_sync(int G, int grp) {
-  if (G <= 32) __syncwarp();
+  if (WARP || G <= 32) __syncwarp();
   else asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(G) : "memory");
 }
 
@@ -244,12 +248,13 @@ __device__ __forceinline__ void group_pass(cplx<T>* x, const cplx<T>* in, cplx<T
 
 // BLOCK: the block's transforms step together and synchronise with
 // __syncthreads (groups whose threads interleave, e.g. column tiles).
-template <typename T, int SIGN, bool TWC = false, bool BLOCK = false>
+// WARP: G <= 32 (see group_sync).
+template <typename T, int SIGN, bool TWC = false, bool BLOCK = false, bool WARP = false>
 __device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int G, int grp, int log2N,
                           const cplx<T>* __restrict__ tw) {
   auto sync = [&]() {
     if (BLOCK) __syncthreads();
-    else group_sync(G, grp);
+    else group_sync<WARP>(G, grp);
   };
   // first pass: radix 8, stride 1, no twiddles; butterfly j takes x[0..7]
   dft8<T, SIGN>(x);

@@ -222,14 +222,14 @@ __device__ __forceinline__ void load_pair_spectrum(cplx<T> (&x)[8], const cplx<T
 // Spectrum Z of p + i q held at the thread's positions -> kx in [0, KXP)
 // halves of p and q, scaled by 1/N, into row `rowoff` of mixed fields da and
 // db (db null: p only).  One exchange through the free buffer.
-template <typename T>
+template <typename T, bool WARP = false>
 __device__ __forceinline__ void store_pair_spectrum(const cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
                                                     cplx<T>* __restrict__ da, cplx<T>* __restrict__ db,
                                                     long long rowoff, int j, int G, int grp, int N, int K, int KXP) {
   cplx<T>* b = w ? buf1 : buf0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) b[sidx<T>(j + m * G)] = x[m];
-  group_sync(G, grp);
+  group_sync<WARP>(G, grp);
   const T h = (T)0.5 / (T)N;
   for (int k = j; k < KXP; k += G) {
     cplx<T> P = mk<T>(0, 0), Q = mk<T>(0, 0);
@@ -353,8 +353,8 @@ __device__ __forceinline__ T bilinear(const T* __restrict__ f, int i, int j, T x
   const unsigned i0 = ((unsigned)i + (unsigned)(int)fx) & msk;
   const unsigned j0 = ((unsigned)j + (unsigned)(int)fy) & msk;
   const unsigned i1 = (i0 + 1u) & msk, j1 = (j0 + 1u) & msk;
-  const T f00 = f[j0 * N + i0], f01 = f[j0 * N + i1];
-  const T f10 = f[j1 * N + i0], f11 = f[j1 * N + i1];
+  const T f00 = __ldg(f + j0 * N + i0), f01 = __ldg(f + j0 * N + i1);
+  const T f10 = __ldg(f + j1 * N + i0), f11 = __ldg(f + j1 * N + i1);
   return ((T)1 - ax) * ((T)1 - ay) * f00 + ax * ((T)1 - ay) * f01 +
          ((T)1 - ax) * ay * f10 + ax * ay * f11;
 }

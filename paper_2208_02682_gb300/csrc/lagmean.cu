@@ -259,6 +259,7 @@ struct BatchExec {
   int64_t launches = 0;
   bool built = false;
   int nstages = 4;  // stages per step of the members' (common) stepper
+  bool warp = false;  // every member's N <= 256: row kernels without named barriers
   std::string err;
 };
 
@@ -330,6 +331,8 @@ static int batch_build_t(BatchExec* b) {
       return SW_EINVAL;
     }
   b->nstages = n > 0 ? stage_count(b->members[0]->p.stepper) : 4;
+  b->warp = true;
+  for (int r = 0; r < n; ++r) b->warp = b->warp && b->members[r]->g.N <= 256;
   // row-pass groups per row: the largest number every member allows (the
   // batch's row-pass blocks all have Bp * Wp * N/8 threads)
   int W = 1 << 20;
@@ -436,7 +439,8 @@ static cudaError_t enqueue_batch_step(BatchExec* b, cudaStream_t s, Prof* pf, in
       const int total = b->start[(size_t)k * (n + 1) + n];
       if (total == 0) continue;
       LAUNCH(SW_K_OF_KT[k], b->bytes[k][stage],
-             launch_stage<T>(k, runs, b->d_start + (size_t)k * (n + 1), n, total, b->threads[k], b->smem[k], stage, s));
+             launch_stage<T>(k, runs, b->d_start + (size_t)k * (n + 1), n, total, b->threads[k], b->smem[k], stage,
+                             b->warp, s));
     }
   }
   return cudaSuccess;

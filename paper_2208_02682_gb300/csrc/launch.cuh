@@ -51,9 +51,11 @@ template <typename T> cudaError_t launch_col_inv(const ColInvArgs<T>& a, cudaStr
 template <typename T> cudaError_t launch_col_fwd(const ColFwdArgs<T>& a, cudaStream_t s);
 template <typename T, typename TO> cudaError_t launch_row_inv(const RowInvArgs<T, TO>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s);
+// warp: every run's rows have N <= 256 (groups of at most one warp), so the
+// row kernels' variant without named barriers may run
 template <typename T>
 cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
-                         size_t smem, int stage, cudaStream_t s);
+                         size_t smem, int stage, bool warp, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s);
@@ -98,8 +100,10 @@ template <typename T> static cudaError_t prepare_kernels_t() {
   if ((e = allow_dynamic_smem(k_row_fwd<T>, mx)) != cudaSuccess) return e;
   if ((e = allow_dynamic_smem(k_stage_col_inv<T>, mx)) != cudaSuccess) return e;
   if ((e = allow_dynamic_smem(k_stage_col_fwd<T>, mx)) != cudaSuccess) return e;
-  if ((e = allow_dynamic_smem(k_stage_row_inv<T>, mx)) != cudaSuccess) return e;
-  if ((e = allow_dynamic_smem(k_stage_row_prod<T>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_inv<T, false>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_inv<T, true>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_prod<T, false>, mx)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem(k_stage_row_prod<T, true>, mx)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -131,12 +135,18 @@ template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStr
 
 template <typename T>
 cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
-                         size_t smem, int stage, cudaStream_t s) {
+                         size_t smem, int stage, bool warp, cudaStream_t s) {
   switch (kt) {
     case KT_COL_INV: k_stage_col_inv<T><<<blocks, threads, smem, s>>>(runs, start, nruns, stage); break;
-    case KT_ROW_INV: k_stage_row_inv<T><<<blocks, threads, smem, s>>>(runs, start, nruns); break;
+    case KT_ROW_INV:
+      if (warp) k_stage_row_inv<T, true><<<blocks, threads, smem, s>>>(runs, start, nruns);
+      else k_stage_row_inv<T, false><<<blocks, threads, smem, s>>>(runs, start, nruns);
+      break;
     case KT_PHYS_Q: k_stage_phys_q<T><<<blocks, threads, 0, s>>>(runs, start, nruns); break;
-    case KT_ROW_PROD: k_stage_row_prod<T><<<blocks, threads, smem, s>>>(runs, start, nruns, stage); break;
+    case KT_ROW_PROD:
+      if (warp) k_stage_row_prod<T, true><<<blocks, threads, smem, s>>>(runs, start, nruns, stage);
+      else k_stage_row_prod<T, false><<<blocks, threads, smem, s>>>(runs, start, nruns, stage);
+      break;
     case KT_COL_FWD: k_stage_col_fwd<T><<<blocks, threads, smem, s>>>(runs, start, nruns); break;
     default: k_stage_update<T><<<blocks, threads, 0, s>>>(runs, start, nruns, stage); break;
   }
@@ -160,7 +170,7 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
   template cudaError_t launch_col_fwd<T>(const ColFwdArgs<T>&, cudaStream_t);                               \
   template cudaError_t launch_row_inv<T, T>(const RowInvArgs<T, T>&, cudaStream_t);                         \
   template cudaError_t launch_row_fwd<T>(const RowFwdArgs<T>&, cudaStream_t);                               \
-  template cudaError_t launch_stage<T>(int, const RunDesc<T>*, const int*, int, int, int, size_t, int,     \
+  template cudaError_t launch_stage<T>(int, const RunDesc<T>*, const int*, int, int, int, size_t, int, bool, \
                                        cudaStream_t);                                                       \
   template cudaError_t launch_spec_to_f64<T>(const cplx<T>*, const cplx<T>*, double2*, long long, int, int,  \
                                              double, cudaStream_t);                                         \

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_stage_col_fwd(const RunDesc<T>* __restr
 
 // a3: Strategy-2 gather buffer (physical u, v | h, zeta), local block =
 // (pair, row block of Bi rows, one row per group of N/8 threads).
-template <typename T>
+template <typename T, bool WARP>
 __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restrict__ runs,
                                                        const int* __restrict__ start, int nruns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
   int w = 0;
   load_pair_spectrum<T>(x, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, (long long)y * g.KXP, j, G, N,
                         g.K);
-  group_fft<T, +1>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
+  group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const long long off = (long long)y * N + j + m * G;
@@ -228,13 +228,13 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 // in FP32, 128 in FP64).
 template <typename T> constexpr int row_prod_max_threads() { return sizeof(T) == 4 ? 384 : 256; }
 
-template <typename T>
+template <typename T, bool WARP>
 __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
                                                                                 const int* __restrict__ start,
                                                                                 int nruns, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
-  const RunDesc<T>& d = runs[r];
+  LM_STAGE_DESC(T);  // field and product lookups from shared memory
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int N = g.N, B = d.Bp, W = d.Wp, G = N >> 3;
@@ -265,6 +265,10 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const T inv_s = s0 ? (T)0 : (T)(1.0 / s);
   const T inv_dx = (T)((double)N / 6.283185307179586476925286766559);
   const cplx<T>* mix = d.mix;
+  // the gather buffer (written by the previous kernel) is read-only here:
+  // non-coherent loads that need not wait for this block's shared-memory stores
+  const T* __restrict__ phys = d.phys;
+  const long long npts = g.np;
   const long long rowoff = (long long)y * g.KXP;
   int w = 0;
   cplx<T> x[8];
@@ -281,12 +285,17 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   int base_a[2], base_b[2], base_o[2];
   int nbase = 0;
   if (s2) {
-    if (wg == 0) {
+    // physical u, v, h, zeta of the row (gather buffer) into U, by the row's
+    // groups other than group 0 (which transforms xi) when there are any
+    const int u0 = W > 1 ? 1 : 0;
+    if (wg >= u0) {
+      for (int f = wg - u0; f < 4; f += W - u0) {
+        const T* __restrict__ src = phys + f * npts + (long long)y * N + j;
+        T v[8];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const long long off = (long long)y * N + j + m * G;
+        for (int m = 0; m < 8; ++m) v[m] = __ldg(src + m * G);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) U[f * N + m * G + j] = d.phys[f * g.np + off];
+        for (int m = 0; m < 8; ++m) U[f * N + m * G + j] = v[m];
       }
     }
     base_a[0] = L.i_xi[0], base_b[0] = L.i_xi[1], base_o[0] = 4;
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   for (int t = wg; t < nbase; t += W) {
     load_pair_spectrum<T>(x, mix + (long long)base_a[t] * g.mi, mix + (long long)base_b[t] * g.mi, rowoff, j, G, N,
                           g.K);
-    group_fft<T, +1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
     T* dst = U + base_o[t] * N;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
       if (kind == PK_ADV || kind == PK_XI || kind == PK_GBAR) {
         load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
                               g.K);
-        group_fft<T, +1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+        group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
       }
       const int pc = L.pc[p];
       T* const pz = PZ + slot * N;
@@ -377,7 +386,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
             const T xx = XI[e], xy = XI[N + e];
             T fi;
             if (kind == PK_XI && kin) fi = pc == 0 ? adv_x : adv_y;
-            else fi = bilinear<T>(d.phys + (long long)pc * g.np, e, y, xx, xy, inv_dx, N);
+            else fi = bilinear<T>(phys + (long long)pc * npts, e, y, xx, xy, inv_dx, N);
             S[e] = fi;
           }
 #pragma unroll
@@ -397,8 +406,8 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
     }
 #pragma unroll
     for (int m = 0; m < 8; ++m) x[m] = mk<T>(PZ[m * G + j], npq == 2 ? PZ[N + m * G + j] : (T)0);
-    group_fft<T, -1>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
-    store_pair_spectrum<T>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
+    group_fft<T, -1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    store_pair_spectrum<T, WARP>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
                            npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, G, gi, N, g.K,
                            g.KXP);
   }
