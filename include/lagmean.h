@@ -199,7 +199,7 @@ int sw_time(sw_handle* h, double* t);
 
 /* Kernel classes reported by sw_kernel_times. */
 #define SW_K_COL_INV 0  /* column pass: spectral -> mixed (derivatives, inverse y-FFT) */
-#define SW_K_ROW_INV 1  /* row pass: mixed -> physical gather buffer (Strategy 2)   */
+#define SW_K_ROW_INV 1  /* row pass: mixed -> physical base fields (u, v, h, zeta, xi) */
 #define SW_K_ROW_PROD 2 /* row pass: inverse x-FFT, products, forward x-FFT        */
 #define SW_K_COL_FWD 3  /* column pass: forward y-FFT and 2/3 mask                  */
 #define SW_K_UPDATE 4   /* right-hand sides and RK4 integrating-factor update       */
@@ -249,7 +249,7 @@ int sw_batch_step(sw_batch* b, int64_t nsteps);
 /* Autotuner: times the row-pass launch shapes (points per block 256, 512,
  * 1024 or 2048, as long as every member fits; product pairs per block 1, 2, 3
  * or all; choice = 4 * points index + pairs index) on trial_steps >= 1
- * replayed steps each, keeps the fastest for all members and returns its
+ * replayed steps each (after as many untimed ones), keeps the fastest for all members and returns its
  * index in *choice (may be NULL).  The members' states are saved before the trials and
  * restored after them (temporary device copies).  Synchronises. */
 int sw_batch_tune(sw_batch* b, int trial_steps, int* choice);

@@ -80,7 +80,7 @@ enum { MAXF = 16, MAXI = 24, MAXP = 16 };
 enum { OP_ID = 0, OP_DX = 1, OP_DY = 2, OP_CURL = 3 };
 enum { LMF_ZETA = 0, LMF_H = 1, LMF_U = 2, LMF_V = 3, LMF_Q = 4, NLMF = 5 };
 // physical fields of the row pass (and of the Strategy-2 gather buffer)
-enum { PH_U = 0, PH_V = 1, PH_H = 2, PH_Z = 3, PH_Q = 4, NPH = 5 };
+enum { PH_U = 0, PH_V = 1, PH_H = 2, PH_Z = 3, PH_Q = 4, PH_XX = 5, PH_XY = 6, NPH = 7 };
 // products formed in physical space by the row pass
 enum {
   PK_ZV = 0,   // zeta v
@@ -134,7 +134,8 @@ struct StepConsts {
   int pad;
 };
 
-// stages per step of a stepper
-__host__ __device__ __forceinline__ int stage_count(int stepper) { return stepper == 0 ? 4 : (stepper == 1 ? 2 : 1); }
+// passes of the stage pipeline per step of a stepper: RK4 4 stages, Heun 2,
+// forward Euler 1 stage and an update-only pass that commits y_{n+1}
+__host__ __device__ __forceinline__ int stage_count(int stepper) { return stepper == 0 ? 4 : 2; }
 
 }  // namespace lm

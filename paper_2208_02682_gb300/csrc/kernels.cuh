@@ -334,9 +334,13 @@ __global__ void __launch_bounds__(256) k_row_fwd(const __grid_constant__ RowFwdA
 // Interval time of a stage: s = (steps done + c_stage) * dt, from the device
 // step counter (never accumulated).
 // time of a stage in steps: RK4 (0, 1/2, 1/2, 1), Heun (0, 1), Euler (0)
-__device__ __forceinline__ double stage_time(const long long* ctr, int stage, double dt, int stepper) {
-  const double c = stage == 0 ? 0.0 : (stepper != 0 || stage == 3 ? 1.0 : 0.5);
-  return ((double)(*ctr) + c) * dt;
+// Computed in the kernel's precision T: sm_103 issues FP64 arithmetic at a
+// small fraction of the FP32 rate, so FP32 kernels keep it out of the set-up
+// every thread runs.
+template <typename T>
+__device__ __forceinline__ T stage_time(const long long* ctr, int stage, T dt, int stepper) {
+  const T c = stage == 0 ? (T)0 : (stepper != 0 || stage == 3 ? (T)1 : (T)0.5);
+  return ((T)(*ctr) + c) * dt;
 }
 
 // Bilinear interpolation of the periodic grid field f at (x_i + xi_x, y_j + xi_y)

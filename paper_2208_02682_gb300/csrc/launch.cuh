@@ -23,7 +23,7 @@ inline int row_block_rows(int N, int points = 512) {
 // Row pass: B rows per block, W groups of N/8 threads per row (see
 // k_stage_row_prod); the block may hold up to row_prod_max_threads threads.
 template <typename T> size_t row_prod_smem(int N, int B, int W, int strategy) {
-  const size_t nur = strategy == 2 ? 6 : 4, nug = strategy == 2 ? 3 : 2;
+  const size_t nur = strategy == 2 ? 6 : 4, nug = (size_t)row_prod_group_rows(strategy, N);
   return (size_t)B * nur * N * sizeof(T) +
          (size_t)B * W * (2 * row_stride<T>(N) * sizeof(cplx<T>) + nug * N * sizeof(T));
 }

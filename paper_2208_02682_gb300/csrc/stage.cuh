@@ -21,6 +21,7 @@ struct RunDesc {
   Geom g;
   Layout L;
   StepConsts c;
+  T cdt, cf0, cc2, cadvx, cadvy;  // dt, f0, c2, adv in the kernels' precision
   cplx<T>* y;     // state at t_n
   cplx<T>* ysa;   // stage inputs of stages 1 and 3
   cplx<T>* ysb;   // stage input of stage 2
@@ -181,8 +182,11 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
   const int rs = row_stride<T>(N);
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
   cplx<T>* buf1 = buf0 + rs;
-  const int ia = pair == 0 ? d.L.i_u : d.L.i_h, ib = pair == 0 ? d.L.i_v : d.L.i_z;
-  const int oa = pair == 0 ? PH_U : PH_H, ob = pair == 0 ? PH_V : PH_Z;
+  // pairs (u, v), (h, zeta) and, Strategy 2, (xi_x, xi_y)
+  const int ia = pair == 0 ? d.L.i_u : (pair == 1 ? d.L.i_h : d.L.i_xi[0]);
+  const int ib = pair == 0 ? d.L.i_v : (pair == 1 ? d.L.i_z : d.L.i_xi[1]);
+  const int oa = pair == 0 ? PH_U : (pair == 1 ? PH_H : PH_XX);
+  const int ob = pair == 0 ? PH_V : (pair == 1 ? PH_Z : PH_XY);
   cplx<T> x[8];
   int w = 0;
   load_pair_spectrum<T>(x, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, (long long)y * g.KXP, j, G, N,
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
   const RunDesc<T>& d = runs[r];
   const long long i = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
   const long long np = d.g.np;
-  if (i < np) d.phys[PH_Q * np + i] = ((T)d.c.f0 + d.phys[PH_Z * np + i]) / ((T)1 + d.phys[PH_H * np + i]);
+  if (i < np) d.phys[PH_Q * np + i] = (d.cf0 + d.phys[PH_Z * np + i]) / ((T)1 + d.phys[PH_H * np + i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,19 +218,26 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 // per row.  Every transform stays in the registers of its group (group_fft):
 // a row's physical values live at the thread's own positions x = j + m G,
 // where the products are formed and the forward transform of each product
-// pair starts.  First the row's base fields (u, v | h, zeta; Strategy 2: xi,
-// with u, v, h, zeta read from the gather buffer) are transformed, the steps
-// shared out over the row's groups, into the row's U; then the groups take
-// the block's product pairs in turn.  Wp > 1 only when a group is a whole
+// pair starts.  First the row's base fields (u, v, h, zeta; Strategy 2: xi),
+// transformed by the row inverse pass, are read into the row's U, the loads
+// shared out over the row's groups; then the groups take the block's product
+// pairs in turn.  Wp > 1 only when a group is a whole
 // number of warps (N >= 256), so groups that do different numbers of
 // transforms never share a warp barrier.
 // Smem: per row U (u, v, h, zeta and, Strategy 2, xi_x, xi_y: N reals each);
 // per group two exchange buffers of row_stride(N) complex, PZ (the two
-// products of a pair) and, Strategy 2, S (gathered values), N reals each.
+// products of a pair) and, Strategy 2, S (the first product's gathered
+// values; the second's are gathered into its PZ row), N reals each.
 
 // Threads per row-pass block at most (two blocks per SM: up to 85 registers
 // in FP32, 128 in FP64).
 template <typename T> constexpr int row_prod_max_threads() { return sizeof(T) == 4 ? 384 : 256; }
+
+// Rows of N reals per group of the row pass besides its exchange buffers:
+// the pair's two products and, Strategy 2, the values gathered at x + xi for
+// the first product (the second product's are gathered into its own row,
+// which the product then overwrites element by element).
+__host__ __device__ __forceinline__ int row_prod_group_rows(int strategy, int) { return strategy == 2 ? 3 : 2; }
 
 template <typename T, bool WARP>
 __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
@@ -246,7 +257,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const int y = rb * B + row;
   const int rs = row_stride<T>(N);
   const bool s2 = L.strategy == 2;
-  const int nur = s2 ? 6 : 4, nug = s2 ? 3 : 2;
+  const int nur = s2 ? 6 : 4, nug = row_prod_group_rows(L.strategy, N);
   T* U = reinterpret_cast<T*>(smem_raw) + (size_t)row * nur * N;
   T* XI = U + 4 * N;
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(reinterpret_cast<T*>(smem_raw) + (size_t)B * nur * N) +
@@ -258,12 +269,12 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const int p0 = pg * d.ppb * 2;
   const int p1 = min(np, p0 + d.ppb * 2);
   const bool kin = L.model == 1;
-  const T adv_x = (T)d.c.adv_x, adv_y = (T)d.c.adv_y;
-  const T f0 = (T)d.c.f0;
-  const double s = stage_time(d.ctr, stage, d.c.dt, d.c.stepper);
-  const bool s0 = !(s > 0.0);
-  const T inv_s = s0 ? (T)0 : (T)(1.0 / s);
-  const T inv_dx = (T)((double)N / 6.283185307179586476925286766559);
+  const T adv_x = d.cadvx, adv_y = d.cadvy;
+  const T f0 = d.cf0;
+  const T s = stage_time<T>(d.ctr, stage, d.cdt, d.c.stepper);
+  const bool s0 = !(s > (T)0);
+  const T inv_s = s0 ? (T)0 : (T)1 / s;
+  const T inv_dx = (T)N / (T)6.283185307179586476925286766559;
   const cplx<T>* mix = d.mix;
   // the gather buffer (written by the previous kernel) is read-only here:
   // non-coherent loads that need not wait for this block's shared-memory stores
@@ -273,24 +284,15 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   int w = 0;
   cplx<T> x[8];
 
-  // which physical base fields this block's products read
-  bool need_uv = false, need_hz = false;
-  for (int p = p0; p < p1; ++p) {
-    const int k = L.pk[p];
-    if (k == PK_ZV || k == PK_ZU || k == PK_HU || k == PK_HV || k == PK_Q) need_hz = true;
-    if (k == PK_ZV || k == PK_ZU || k == PK_KE || k == PK_HU || k == PK_HV) need_uv = true;
-    if ((k == PK_ADV || k == PK_XI || k == PK_GBAR) && !kin) need_uv = true;
-  }
-  // base fields of the row into U (and XI)
-  int base_a[2], base_b[2], base_o[2];
-  int nbase = 0;
-  if (s2) {
-    // physical u, v, h, zeta of the row (gather buffer) into U, by the row's
-    // groups other than group 0 (which transforms xi) when there are any
-    const int u0 = W > 1 ? 1 : 0;
-    if (wg >= u0) {
-      for (int f = wg - u0; f < 4; f += W - u0) {
-        const T* __restrict__ src = phys + f * npts + (long long)y * N + j;
+  // the row's physical u, v, h, zeta (and, Strategy 2, xi_x, xi_y), written
+  // by the row inverse pass, into U (and XI = U + 4N), shared out over the
+  // row's groups
+  {
+    const int nplanes = s2 ? 6 : 4;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      if (f < nplanes && f % W == wg) {
+        const T* __restrict__ src = phys + (long long)(f < 4 ? f : f + 1) * npts + (long long)y * N + j;
         T v[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = __ldg(src + m * G);
@@ -298,36 +300,49 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
         for (int m = 0; m < 8; ++m) U[f * N + m * G + j] = v[m];
       }
     }
-    base_a[0] = L.i_xi[0], base_b[0] = L.i_xi[1], base_o[0] = 4;
-    nbase = 1;
-  } else {
-    if (need_uv) base_a[nbase] = L.i_u, base_b[nbase] = L.i_v, base_o[nbase] = 0, ++nbase;
-    if (need_hz) base_a[nbase] = L.i_h, base_b[nbase] = L.i_z, base_o[nbase] = 2, ++nbase;
   }
-  for (int t = wg; t < nbase; t += W) {
-    load_pair_spectrum<T>(x, mix + (long long)base_a[t] * g.mi, mix + (long long)base_b[t] * g.mi, rowoff, j, G, N,
-                          g.K);
-    group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
-    T* dst = U + base_o[t] * N;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      dst[m * G + j] = x[m].x;
-      dst[N + m * G + j] = x[m].y;
-    }
-  }
+
+  // the gradient spectrum of a product, into the registers x; the first
+  // product of the group's first pair is loaded before the wait for the row's
+  // base fields
+  const int npair = (p1 - p0 + 1) >> 1;
+  auto load_grad = [&](int p) {
+    const int k = L.pk[p];
+    if (k == PK_ADV || k == PK_XI || k == PK_GBAR)
+      load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
+                            g.K);
+  };
+  if (wg < npair) load_grad(p0 + 2 * wg);
   __syncthreads();
 
+  // Strategy 2: the values at x + xi (Eqs. xi_evol, barf_xi) that product p
+  // needs, by bilinear interpolation into dst (N reals)
+  auto gather = [&](int p, T* dst) {
+    const int kind = L.pk[p], pc = L.pc[p];
+    if (kind != PK_GBAR && (kind != PK_XI || kin)) return;
+    const T* __restrict__ src = phys + (long long)pc * npts;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int e = m * G + j;
+      dst[e] = bilinear<T>(src, e, y, XI[e], XI[N + e], inv_dx, N);
+    }
+  };
+
   // product pairs, shared out over the row's groups
-  const int npair = (p1 - p0 + 1) >> 1;
   for (int q = wg; q < npair; q += W) {
     const int pa = p0 + 2 * q;
     const int npq = min(2, p1 - pa);
+    if (q != wg) load_grad(pa);
+    if (s2) {
+      // both products' gathers, issued together
+      gather(pa, S);
+      if (npq == 2) gather(pa + 1, PZ + N);
+    }
     for (int slot = 0; slot < npq; ++slot) {
       const int p = pa + slot;
       const int kind = L.pk[p];
+      if (slot == 1) load_grad(p);
       if (kind == PK_ADV || kind == PK_XI || kind == PK_GBAR) {
-        load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
-                              g.K);
         group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
       }
       const int pc = L.pc[p];
@@ -377,18 +392,8 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
           }
           break;
         default: {
-          // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0.
-          // The gathered values go through the thread's own slots of S first,
-          // so that only a few of the bilinear loads are in flight per thread.
-#pragma unroll 1
-          for (int m = 0; m < 8; ++m) {
-            const int e = m * G + j;
-            const T xx = XI[e], xy = XI[N + e];
-            T fi;
-            if (kind == PK_XI && kin) fi = pc == 0 ? adv_x : adv_y;
-            else fi = bilinear<T>(phys + (long long)pc * npts, e, y, xx, xy, inv_dx, N);
-            S[e] = fi;
-          }
+          // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0
+          const T* const sv = slot == 0 ? S : PZ + N;
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int e = m * G + j;
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
             const T wx = s0 ? (T)0.5 * ua : xx * inv_s;
             const T wy = s0 ? (T)0.5 * va : xy * inv_s;
             const T wgrad = wx * x[m].x + wy * x[m].y;
-            const T fi = S[e];
+            const T fi = (kind == PK_XI && kin) ? (pc == 0 ? adv_x : adv_y) : sv[e];
             put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wgrad : fi - wgrad);
           }
           break;
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
 
 // ---------------------------------------------------------------------------
 // a4 (second half): right-hand sides and RK4 with integrating factor, one
-// thread per (mode, evolved field); local block = (field, mode block).
+// thread per (evolved field, two modes); local block = (field, mode block).
 //   stage 0: a = N(y_n)      acc = E^2 a            y1 = E (y_n + dt/2 a)
 //   stage 1: b = N(y1)       acc += 2 E b           y2 = E y_n + dt/2 b
 //   stage 2: c = N(y2)       acc += 2 E c           y3 = E^2 y_n + dt E c
@@ -436,15 +441,45 @@ __device__ __forceinline__ double kahan_add_rn(double sum, double add, double& c
   return t;
 }
 
+// y_{n+1} = E^2 y_n + inc at element o of field f (compensated in FP32 for
+// the fields marked so).
+template <typename T>
+__device__ __forceinline__ void commit_mode(const RunDesc<T>& d, int f, long long o, T E, cplx<T> inc) {
+  const cplx<T> yn = d.y[o];
+  const T E2 = E * E;
+  if (d.comp && d.L.fkahan[f]) {
+    cplx<T> cc = d.comp[o];
+    cc.x *= E2;
+    cc.y *= E2;
+    cplx<T> out;
+    out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
+    out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
+    d.y[o] = out;
+    d.comp[o] = cc;
+  } else {
+    d.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
+  }
+}
+
 // Right-hand side and RK4 update of evolved field f at mode m = kyi*KXP + kx
 // (kx <= K); prod(p) returns the spectral product p at this mode.
 template <typename T, typename PF>
-__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, double sd, int f, long long m, int kx,
+__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd, int f, long long m, int kx,
                                             int kyi, PF prod) {
   const Geom& g = d.g;
   const Layout& L = d.L;
+  const int st = d.c.stepper;
+  const int cls = L.fclass[f];
+  const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
+  const long long o = f * g.ms + m;
+  if (st == 2 && stage == 1) {
+    // forward Euler, second pass: y_{n+1} = E^2 y_n + dt E^2 a, the increment
+    // from the first pass (a separate pass: the first reads other fields' y_n)
+    commit_mode<T>(d, f, o, E, d.acc[o]);
+    return;
+  }
   const T kxf = (T)kx, kyf = (T)(kyi - g.K);
-  const T dt = (T)d.c.dt;
+  const T dt = d.cdt;
   const cplx<T>* yin = stage_input(d, stage);
   const int role = L.frole[f], slot = L.fslot[f];
   cplx<T> rhs;
@@ -455,14 +490,14 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, doub
         rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(prod(L.p_hu), kxf), cik<T>(prod(L.p_hv), kyf)));
       } else {
         const cplx<T> hh = yin[L.f_h * g.ms + m];
-        const cplx<T> Bq = cadd<T>(cscale<T>(hh, (T)d.c.c2), prod(L.p_ke));
+        const cplx<T> Bq = cadd<T>(cscale<T>(hh, d.cc2), prod(L.p_ke));
         if (role == R_U)
-          rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], (T)d.c.f0), prod(L.p_zv)), cik<T>(Bq, kxf));
+          rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], d.cf0), prod(L.p_zv)), cik<T>(Bq, kxf));
         else
-          rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -(T)d.c.f0), prod(L.p_zu)), cik<T>(Bq, kyf));
+          rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -d.cf0), prod(L.p_zu)), cik<T>(Bq, kyf));
       }
     } else {
-      const T kc = kxf * (T)d.c.adv_x + kyf * (T)d.c.adv_y;
+      const T kc = kxf * d.cadvx + kyf * d.cadvy;
       rhs = cik<T>(yin[f * g.ms + m], -kc);
     }
   } else if (role == R_P) {
@@ -472,7 +507,7 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, doub
       cplx<T> ua;
       if (L.model == 1) {
         const bool k0 = (kx == 0 && kyi == g.K);
-        ua = mk<T>(k0 ? (T)(slot == 0 ? d.c.adv_x : d.c.adv_y) : (T)0, 0);
+        ua = mk<T>(k0 ? (slot == 0 ? d.cadvx : d.cadvy) : (T)0, 0);
       } else {
         ua = yin[(slot == 0 ? L.f_u : L.f_v) * g.ms + m];
       }
@@ -497,14 +532,13 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, doub
       rhs = L.strategy == 1 ? csub<T>(fh, pg) : pg;
     }
   }
-  const int cls = L.fclass[f];
-  const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
-  const long long o = f * g.ms + m;
   const cplx<T> yn = d.y[o];
   cplx<T>* yout = stage == 1 ? d.ysb : d.ysa;
-  const int st = d.c.stepper;
   const bool last = stage == stage_count(st) - 1;
-  if (!last && st != 0) {
+  if (st == 2) {
+    // forward Euler, first pass: the increment dt E^2 a
+    d.acc[o] = cscale<T>(rhs, dt * E * E);
+  } else if (!last && st != 0) {
     // Heun, stage 0: acc = E^2 a, y1 = E^2 (y_n + dt a)
     d.acc[o] = cscale<T>(rhs, E * E);
     yout[o] = cscale<T>(cadd<T>(yn, cscale<T>(rhs, dt)), E * E);
@@ -518,25 +552,15 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, doub
     d.acc[o] = cadd<T>(d.acc[o], cscale<T>(rhs, (T)2 * E));
     yout[o] = cadd<T>(cscale<T>(yn, E * E), cscale<T>(rhs, dt * E));
   } else {
-    // final stage: y_{n+1} = E^2 y_n + inc, with inc = dt/6 (acc + d) (RK4),
-    // dt/2 (acc + b) (Heun) or dt E^2 a (forward Euler)
-    const T E2 = E * E;
-    const cplx<T> inc = st == 0 ? cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)6)
-                                : (st == 1 ? cscale<T>(cadd<T>(d.acc[o], rhs), dt / (T)2) : cscale<T>(rhs, dt * E2));
-    if (d.comp && L.fkahan[f]) {
-      cplx<T> cc = d.comp[o];
-      cc.x *= E2;
-      cc.y *= E2;
-      cplx<T> out;
-      out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
-      out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
-      d.y[o] = out;
-      d.comp[o] = cc;
-    } else {
-      d.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
-    }
+    // final stage: y_{n+1} = E^2 y_n + inc, with inc = dt/6 (acc + d) (RK4)
+    // or dt/2 (acc + b) (Heun); its inputs are the stage buffers, not y
+    commit_mode<T>(d, f, o, E, cscale<T>(cadd<T>(d.acc[o], rhs), st == 0 ? dt / (T)6 : dt / (T)2));
   }
 }
+
+// Modes per block of the update kernel (two per thread: the grid of a
+// 256^2 Strategy-1 + Strategy-2 batch then fits in one wave of blocks).
+constexpr int UPD_MODES = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restrict__ runs,
@@ -546,14 +570,18 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int lb = blockIdx.x - start[r];
-  const int mblocks = (int)((g.ms + 255) / 256);
+  const int mblocks = (int)((g.ms + UPD_MODES - 1) / UPD_MODES);
   const int f = lb / mblocks;
-  const long long m = (long long)(lb - f * mblocks) * 256 + threadIdx.x;
-  const double sd = stage_time(d.ctr, stage, d.c.dt, d.c.stepper);
-  if (m < g.ms) {
-    const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
-    if (kx <= g.K) {
-      update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
+  const long long m0 = (long long)(lb - f * mblocks) * UPD_MODES + threadIdx.x;
+  const T sd = stage_time<T>(d.ctr, stage, d.cdt, d.c.stepper);
+#pragma unroll
+  for (int u = 0; u < UPD_MODES / 256; ++u) {
+    const long long m = m0 + u * 256;
+    if (m < g.ms) {
+      const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
+      if (kx <= g.K) {
+        update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
+      }
     }
   }
   if (stage == stage_count(d.c.stepper) - 1) {

@@ -8,6 +8,8 @@
 * A batch runs one stepper (mixed batches are refused); a batch of Heun
   runs matches its members run alone bit for bit; a server that mixes
   steppers batches them apart and each job matches its run alone.
+* Repeated runs agree bit for bit (forward Euler's single stage reads the
+  state it updates, so its update is committed in a separate pass).
 """
 import time
 
@@ -164,3 +166,27 @@ def test_server_mixes_steppers(lm):
         lm.sw_destroy(h)
         for k in ref:
             assert np.array_equal(d["out"][k], ref[k]), (d["tag"], k)
+
+
+@pytest.mark.parametrize("stepper", ["euler", "heun", "rk4"])
+def test_repeated_runs_are_bitwise_equal(lm, stepper):
+    # a step must never read a state element that another thread of the same
+    # pass overwrites: two identical runs (and a run split into chunks) agree
+    # bit for bit
+    N, n = 128, 12
+    ic = np.ascontiguousarray(np.stack(turbulence(N, seed=77)))
+    outs = []
+    for chunks in ([n], [n], [5, 7]):
+        h = lm.sw_create(lm.make_params(N, 5e-3, precision="f32", nu8=_nu("hyper8", N), stepper=stepper), ic)
+        try:
+            lm.lmean_begin(h, lm.make_lm_params(1, ("zeta", "h", "u", "v"), n_steps=n))
+            for c in chunks:
+                lm.lmean_step(h, c)
+            out = {k: np.zeros((N, N)) for k in ("zeta", "h", "u", "v", "pos_x", "pos_y")}
+            lm.lmean_end(h, out)
+        finally:
+            lm.sw_destroy(h)
+        outs.append(out)
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
