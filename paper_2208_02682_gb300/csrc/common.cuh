@@ -134,6 +134,16 @@ struct StepConsts {
   int pad;
 };
 
+// Programmatic dependent launch (PTX griddepcontrol).  The stage kernels of
+// a step are launched with programmatic stream serialisation, so a kernel's
+// blocks may start while the previous kernel of the stream finishes.
+// pdl_wait: before its first access to memory that earlier kernels write,
+// a stage kernel waits until they have completed and their writes are
+// visible (without the launch attribute it returns at once).  pdl_release:
+// after its last store, the kernel lets the next one be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // passes of the stage pipeline per step of a stepper: RK4 4 stages, Heun 2,
 // forward Euler 1 stage and an update-only pass that commits y_{n+1}
 __host__ __device__ __forceinline__ int stage_count(int stepper) { return stepper == 0 ? 4 : 2; }

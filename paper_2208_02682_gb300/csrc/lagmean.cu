@@ -491,7 +491,7 @@ static cudaError_t enqueue_batch_step(BatchExec* b, cudaStream_t s, Prof* pf, in
       if (total == 0) continue;
       LAUNCH(SW_K_OF_KT[k], b->bytes[k][stage],
              launch_stage<T>(k, runs, b->d_start + (size_t)k * (n + 1), n, total, b->threads[k], b->smem[k], stage,
-                             b->warp, s));
+                             b->warp, pf == nullptr, s));
     }
   }
   return cudaSuccess;

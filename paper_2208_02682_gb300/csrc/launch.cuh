@@ -52,10 +52,11 @@ template <typename T> cudaError_t launch_col_fwd(const ColFwdArgs<T>& a, cudaStr
 template <typename T, typename TO> cudaError_t launch_row_inv(const RowInvArgs<T, TO>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s);
 // warp: every run's rows have N <= 256 (groups of at most one warp), so the
-// row kernels' variant without named barriers may run
+// row kernels' variant without named barriers may run.  pdl: launch with
+// programmatic stream serialisation (see pdl_wait).
 template <typename T>
 cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
-                         size_t smem, int stage, bool warp, cudaStream_t s);
+                         size_t smem, int stage, bool warp, bool pdl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s);
@@ -135,22 +136,29 @@ template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStr
 
 template <typename T>
 cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
-                         size_t smem, int stage, bool warp, cudaStream_t s) {
+                         size_t smem, int stage, bool warp, bool pdl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
   switch (kt) {
-    case KT_COL_INV: k_stage_col_inv<T><<<blocks, threads, smem, s>>>(runs, start, nruns, stage); break;
+    case KT_COL_INV: return cudaLaunchKernelEx(&cfg, k_stage_col_inv<T>, runs, start, nruns, stage);
     case KT_ROW_INV:
-      if (warp) k_stage_row_inv<T, true><<<blocks, threads, smem, s>>>(runs, start, nruns);
-      else k_stage_row_inv<T, false><<<blocks, threads, smem, s>>>(runs, start, nruns);
-      break;
-    case KT_PHYS_Q: k_stage_phys_q<T><<<blocks, threads, 0, s>>>(runs, start, nruns); break;
+      return warp ? cudaLaunchKernelEx(&cfg, k_stage_row_inv<T, true>, runs, start, nruns)
+                  : cudaLaunchKernelEx(&cfg, k_stage_row_inv<T, false>, runs, start, nruns);
+    case KT_PHYS_Q: cfg.dynamicSmemBytes = 0; return cudaLaunchKernelEx(&cfg, k_stage_phys_q<T>, runs, start, nruns);
     case KT_ROW_PROD:
-      if (warp) k_stage_row_prod<T, true><<<blocks, threads, smem, s>>>(runs, start, nruns, stage);
-      else k_stage_row_prod<T, false><<<blocks, threads, smem, s>>>(runs, start, nruns, stage);
-      break;
-    case KT_COL_FWD: k_stage_col_fwd<T><<<blocks, threads, smem, s>>>(runs, start, nruns); break;
-    default: k_stage_update<T><<<blocks, threads, 0, s>>>(runs, start, nruns, stage); break;
+      return warp ? cudaLaunchKernelEx(&cfg, k_stage_row_prod<T, true>, runs, start, nruns, stage)
+                  : cudaLaunchKernelEx(&cfg, k_stage_row_prod<T, false>, runs, start, nruns, stage);
+    case KT_COL_FWD: return cudaLaunchKernelEx(&cfg, k_stage_col_fwd<T>, runs, start, nruns);
+    default: cfg.dynamicSmemBytes = 0; return cudaLaunchKernelEx(&cfg, k_stage_update<T>, runs, start, nruns, stage);
   }
-  return cudaGetLastError();
 }
 
 template <typename T>
@@ -170,8 +178,8 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
   template cudaError_t launch_col_fwd<T>(const ColFwdArgs<T>&, cudaStream_t);                               \
   template cudaError_t launch_row_inv<T, T>(const RowInvArgs<T, T>&, cudaStream_t);                         \
   template cudaError_t launch_row_fwd<T>(const RowFwdArgs<T>&, cudaStream_t);                               \
-  template cudaError_t launch_stage<T>(int, const RunDesc<T>*, const int*, int, int, int, size_t, int, bool, \
-                                       cudaStream_t);                                                       \
+  template cudaError_t launch_stage<T>(int, const RunDesc<T>*, const int*, int, int, int, size_t, int, bool,  \
+                                       bool, cudaStream_t);                                                 \
   template cudaError_t launch_spec_to_f64<T>(const cplx<T>*, const cplx<T>*, double2*, long long, int, int,  \
                                              double, cudaStream_t);                                         \
   template cudaError_t launch_spec_from_f64<T>(const double2*, cplx<T>*, long long, cudaStream_t);

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256) k_stage_col_inv(const RunDesc<T>* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  pdl_wait();  // state written by the previous kernels: only after this
   const Geom& g = d.g;
   const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
   const int lC = d.lC, C = 1 << lC;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(256) k_stage_col_inv(const RunDesc<T>* __restr
   cplx<T>* dst = d.mix + (long long)o * g.mi + kx;
 #pragma unroll
   for (int m = 0; m < 8; ++m) dst[(long long)(j + m * G) * KXP] = x[m];
+  pdl_release();
 }
 
 // a4 (first half): column forward pass of the products, local block =
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(256) k_stage_col_fwd(const RunDesc<T>* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  pdl_wait();  // state written by the previous kernels: only after this
   const Geom& g = d.g;
   const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
   const int lC = d.lC, C = 1 << lC;
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(256) k_stage_col_fwd(const RunDesc<T>* __restr
       dst[(long long)(ky + K) * KXP] = kx <= K ? cscale<T>(x[m], inv) : mk<T>(0, 0);
     }
   }
+  pdl_release();
 }
 
 // a3: Strategy-2 gather buffer (physical u, v | h, zeta), local block =
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  pdl_wait();  // state written by the previous kernels: only after this
   const Geom& g = d.g;
   const int N = g.N, G = N >> 3, B = d.Bi;
   const int lb = blockIdx.x - start[r];
@@ -198,6 +203,7 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
     d.phys[oa * g.np + off] = x[m].x;
     d.phys[ob * g.np + off] = x[m].y;
   }
+  pdl_release();
 }
 
 // q = (f0 + zeta)/h, h = 1 + eta, into the gather buffer (Strategy 2 with PV
@@ -207,9 +213,11 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
                                                       const int* __restrict__ start, int nruns) {
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
+  pdl_wait();  // state written by the previous kernels: only after this
   const long long i = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
   const long long np = d.g.np;
   if (i < np) d.phys[PH_Q * np + i] = (d.cf0 + d.phys[PH_Z * np + i]) / ((T)1 + d.phys[PH_H * np + i]);
+  pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
   LM_STAGE_DESC(T);  // field and product lookups from shared memory
+  pdl_wait();  // state written by the previous kernels: only after this
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int N = g.N, B = d.Bp, W = d.Wp, G = N >> 3;
@@ -416,6 +425,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
                            npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, G, gi, N, g.K,
                            g.KXP);
   }
+  pdl_release();
 }
 
 // ---------------------------------------------------------------------------
@@ -567,6 +577,7 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
                                                       const int* __restrict__ start, int nruns, int stage) {
   const int r = find_run(start, nruns, blockIdx.x);
   LM_STAGE_DESC(T);  // many field lookups per thread: read from shared memory
+  pdl_wait();  // state written by the previous kernels: only after this
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int lb = blockIdx.x - start[r];
@@ -598,6 +609,7 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
       }
     }
   }
+  pdl_release();
 }
 
 }  // namespace lm
