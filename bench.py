@@ -452,10 +452,11 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1
 
 # DRAM bytes per launch of the dominant kernel, from one ncu capture of this
 # bench's timed region (profiles/traffic_rowprod_bench256.md: mean of the warm
-# launches); valid only while the stage-kernel sources are those of that
-# capture (the hash is refreshed with each capture).
-TRAFFIC_CAPTURE = {"kernel": "row_prod", "bytes": 228900.0,
-                   "sources_sha256": "3dfda3670cec127fea28bd66d9f62906867e9e73f4ccc9c821c4a4ec7381da18"}
+# launches, each covering both runs of the batch); valid only while the
+# stage-kernel sources are those of that capture (the hash is refreshed with
+# each capture).
+TRAFFIC_CAPTURE = {"kernel": "row_prod", "bytes": 266715.4, "runs_per_launch": 2,
+                   "sources_sha256": "230081ea256cb87de57105f4e99a113138752db2c8c20ed612d29cb5047b8dc5"}
 
 
 # the sources that define the stage kernels and their launch shapes
@@ -474,10 +475,12 @@ def kernel_sources_sha256():
 
 
 def measured_traffic(kernel):
+    """Per launch of one run, like `achieved` (the captured batched launch
+    covers runs_per_launch runs)."""
     c = TRAFFIC_CAPTURE
     if kernel != c["kernel"] or kernel_sources_sha256() != c["sources_sha256"]:
         return None
-    return c["bytes"]
+    return c["bytes"] / c["runs_per_launch"]
 
 
 def run_ours(args):

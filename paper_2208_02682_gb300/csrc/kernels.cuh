@@ -337,10 +337,14 @@ __global__ void __launch_bounds__(256) k_row_fwd(const __grid_constant__ RowFwdA
 // Computed in the kernel's precision T: sm_103 issues FP64 arithmetic at a
 // small fraction of the FP32 rate, so FP32 kernels keep it out of the set-up
 // every thread runs.
+// The 64-bit step count is converted through its two 31-bit halves (exact
+// in FP64 below 2^53 steps, and in FP32 below 2^24).
 template <typename T>
 __device__ __forceinline__ T stage_time(const long long* ctr, int stage, T dt, int stepper) {
+  const long long n = *ctr;
+  const T steps = (T)(int)(n >> 31) * (T)2147483648.0 + (T)(int)(n & 0x7fffffffLL);
   const T c = stage == 0 ? (T)0 : (stepper != 0 || stage == 3 ? (T)1 : (T)0.5);
-  return ((T)(*ctr) + c) * dt;
+  return (steps + c) * dt;
 }
 
 // Bilinear interpolation of the periodic grid field f at (x_i + xi_x, y_j + xi_y)

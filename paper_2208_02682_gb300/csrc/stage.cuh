@@ -589,7 +589,10 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
   for (int u = 0; u < UPD_MODES / 256; ++u) {
     const long long m = m0 + u * 256;
     if (m < g.ms) {
-      const int kyi = (int)(m / g.KXP), kx = (int)(m - (long long)kyi * g.KXP);
+      // modes of a run fit in 32 bits: 32-bit division (64-bit division is a
+      // long software sequence)
+      const int mi = (int)m;
+      const int kyi = mi / g.KXP, kx = mi - kyi * g.KXP;
       if (kx <= g.K) {
         update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
       }
