@@ -86,6 +86,8 @@ class SLInterval:
         self.interp = interp_linear if interp == "linear" else interp_cubic
         self.n_steps = n_steps
         self.done = 0
+        if oracle.model == "euler2d" and ("h" in self.fields or "q" in self.fields):
+            raise ValueError("euler2d averages zeta, u and v only")
         N = oracle.N
         self.g = {f: np.zeros((N, N)) for f in self.fields}
         self.D = [np.zeros((N, N)), np.zeros((N, N))]
@@ -100,6 +102,8 @@ class SLInterval:
     def _fields(self):
         o = self.o
         u, v, h = o.fields()
+        if o.model == "euler2d":
+            return {"u": u, "v": v, "zeta": h}  # the third field is the vorticity
         zeta = o.phys(o.dx(o.vh) - o.dy(o.uh))
         return {"u": u, "v": v, "h": h, "zeta": zeta, "q": (o.f0 + zeta) / h}
 

@@ -13,6 +13,11 @@ arXiv 2208.02682) it follows.
 
 What is computed (one averaging interval [tau, tau+T], Sec. 2, Eq. (ave)):
 
+* (model "euler2d") two-dimensional incompressible inviscid flow, the test
+  flow of Sec. 4.1: the vorticity zeta is carried in the depth slot and
+  obeys d_t zeta + div(u zeta) = 0, with the velocity slaved to it through
+  the streamfunction (lap psi = zeta, u = -d_y psi, v = d_x psi); the mean of
+  zeta, which no periodic velocity carries, is kept and conserved;
 * the shallow-water dynamics, Sec. 4.2, Eq. (sw_eqs_dimless), written with
   f0 = 1/Ro and c2 = g H = 1/Fr^2, for the depth perturbation eta = h - 1
   (the mean depth is the scale H, so h = 1 + eta; carrying eta instead of h
@@ -76,7 +81,7 @@ class SWOracle:
         self.c2 = float(c2)
         self.nu8 = float(nu8)
         self.lm_nu8 = float(nu8 if lm_nu8 is None else lm_nu8)
-        if model not in ("sw", "kinematic"):
+        if model not in ("sw", "kinematic", "euler2d"):
             raise ValueError(model)
         self.model = model
         self.adv = (float(adv[0]), float(adv[1]))
@@ -96,9 +101,14 @@ class SWOracle:
         self.t = 0.0
         self.uh = self.spec(np.asarray(u, dtype=np.float64))
         self.vh = self.spec(np.asarray(v, dtype=np.float64))
-        # depth perturbation eta = h - 1 (spectral)
-        self.hh = self.spec(np.asarray(h, dtype=np.float64))
-        self.hh[0, 0] -= 1.0
+        if model == "euler2d":
+            # the third field is the vorticity; u and v follow from it
+            self.hh = self.spec(np.asarray(h, dtype=np.float64))
+            self.uh, self.vh = self.velocity_from_vorticity(self.hh)
+        else:
+            # depth perturbation eta = h - 1 (spectral)
+            self.hh = self.spec(np.asarray(h, dtype=np.float64))
+            self.hh[0, 0] -= 1.0
         self.lm = None
 
     # -- transforms --------------------------------------------------------
@@ -109,6 +119,15 @@ class SWOracle:
     def phys(self, F):
         """Spectral -> physical values on the N x N grid."""
         return np.fft.irfft2(F, s=(self.N, self.N)) * float(self.N * self.N)
+
+    def velocity_from_vorticity(self, zh):
+        """Streamfunction psi with lap psi = zeta (zero mean): psi_hat =
+        -zeta_hat/|k|^2, u = -d_y psi, v = d_x psi, i.e. u_hat = i ky zeta_hat/|k|^2
+        and v_hat = -i kx zeta_hat/|k|^2 (zero at k = 0)."""
+        inv = np.zeros_like(self.k2)
+        nz = self.k2 > 0
+        inv[nz] = 1.0 / self.k2[nz]
+        return 1j * self.ky * zh * inv, -1j * self.kx * zh * inv
 
     def dx(self, F):
         return 1j * self.kx * F
@@ -150,6 +169,8 @@ class SWOracle:
         if strategy not in (1, 2):
             raise ValueError("strategy must be 1 or 2")
         fields = tuple(f for f in LM_FIELDS if f in fields)
+        if self.model == "euler2d" and ("h" in fields or "q" in fields):
+            raise ValueError("euler2d averages zeta, u and v only")
         if strategy == 2:
             pos = True  # xi is part of the Strategy-2 dynamics
         z = lambda: np.zeros_like(self.uh)
@@ -164,14 +185,25 @@ class SWOracle:
         """Right-hand sides of all evolved fields at interval time s = t - tau."""
         if self._stage_hook is not None:
             self._stage_hook(st)
-        uh, vh, hh = st["sw"]  # hh: depth perturbation eta
-        zh = self.dx(vh) - self.dy(uh)
+        uh, vh, hh = st["sw"]  # hh: depth perturbation eta (euler2d: vorticity)
+        if self.model == "euler2d":
+            uh, vh = self.velocity_from_vorticity(hh)
+            zh = hh
+        else:
+            zh = self.dx(vh) - self.dy(uh)
         u = self.phys(uh)
         v = self.phys(vh)
         eta = self.phys(hh)
         zeta = self.phys(zh)
         out = {}
-        if self.model == "sw":
+        if self.model == "euler2d":
+            # vorticity equation of Sec. 4.1's test flow: d_t zeta = -div(u zeta);
+            # u and v take no tendency of their own (they follow zeta)
+            Nh = -self.dx(self.spec(u * zeta)) - self.dy(self.spec(v * zeta))
+            Nu, Nv = np.zeros_like(uh), np.zeros_like(vh)
+            au, av = u, v
+            uh_adv, vh_adv = uh, vh
+        elif self.model == "sw":
             # Eq. (sw_momentum_dimless), (sw_mass_dimless), vector-invariant form;
             # grad h = grad eta and h u = u + eta u.
             B = self.c2 * hh + self.spec(0.5 * (u * u + v * v))
@@ -305,6 +337,8 @@ class SWOracle:
 
     def _commit(self, yn):
         self.uh, self.vh, self.hh = yn["sw"]
+        if self.model == "euler2d":
+            self.uh, self.vh = self.velocity_from_vorticity(self.hh)
         if self.lm is not None:
             self.lm["G"] = yn["G"]
             if "P" in yn:
@@ -329,6 +363,8 @@ class SWOracle:
                e * e * yy + (dt / 6.0) * (e * e * aa + 2.0 * e * (bb + cc) + dd),
                y, a, b, c, d, E)
         self.uh, self.vh, self.hh = yn["sw"]
+        if self.model == "euler2d":
+            self.uh, self.vh = self.velocity_from_vorticity(self.hh)
         if self.lm is not None:
             self.lm["G"] = yn["G"]
             if "P" in yn:
@@ -389,11 +425,19 @@ class SWOracle:
 
     # -- diagnostics -------------------------------------------------------
     def fields(self):
+        """Physical u, v, h (euler2d: u, v, zeta)."""
+        if self.model == "euler2d":
+            return self.phys(self.uh), self.phys(self.vh), self.phys(self.hh)
         return self.phys(self.uh), self.phys(self.vh), 1.0 + self.phys(self.hh)
 
     def diag(self):
         """Domain means: mass <h>, energy <h|u|^2/2 + c2 h^2/2>, potential
-        enstrophy <h q^2/2> with q = (f0 + zeta)/h."""
+        enstrophy <h q^2/2> with q = (f0 + zeta)/h.  euler2d: mean vorticity,
+        kinetic energy <|u|^2/2> and enstrophy <zeta^2/2>."""
+        if self.model == "euler2d":
+            u, v, zeta = self.fields()
+            return (float(np.mean(zeta)), float(np.mean(0.5 * (u * u + v * v))),
+                    float(np.mean(0.5 * zeta * zeta)))
         u, v, h = self.fields()
         zeta = self.phys(self.dx(self.vh) - self.dy(self.uh))
         q = (self.f0 + zeta) / h

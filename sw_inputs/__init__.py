@@ -34,6 +34,7 @@ __all__ = [
     "turbulence_plus_waves",
     "mode1_wave",
     "uniform_flow",
+    "vortex_pair",
     "random_smooth_field",
     "smooth_flow",
     "wave_frequency",
@@ -166,6 +167,19 @@ def mode1_wave(N: int, a: float, f0: float, c2: float, t: float = 0.0):
     x = 2.0 * np.pi * np.arange(N) / N
     th = np.broadcast_to(x[None, :] - om * t, (N, N))
     return a * np.cos(th), (a * f0 / om) * np.sin(th), 1.0 + (a / om) * np.cos(th)
+
+
+def vortex_pair(N: int):
+    """Initial vorticity of Sec. 4.1's two-dimensional test flow: two
+    like-signed Gaussian vortices that merge, exp(-(x - pi + 0.1)^2 - (y - pi +
+    pi/3)^2) + exp(-(x - pi - 0.1)^2 - (y - pi - pi/3)^2) on [0, 2 pi)^2.
+    Returns (u, v, zeta) with u = v = 0 placeholders (the two-dimensional
+    Euler model derives the velocity from zeta)."""
+    x = 2.0 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    zeta = (np.exp(-(X - np.pi + 0.1) ** 2 - (Y - np.pi + np.pi / 3) ** 2)
+            + np.exp(-(X - np.pi - 0.1) ** 2 - (Y - np.pi - np.pi / 3) ** 2))
+    return np.zeros((N, N)), np.zeros((N, N)), zeta
 
 
 def uniform_flow(N: int, U0: float, V0: float, h0: float = 1.0):
