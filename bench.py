@@ -407,6 +407,43 @@ def measure_semi_lagrangian(lm, torch):
             "workload": "plain-256 interval, FP32 dynamics, trapezoid + cubic interpolation, FP64 means"}
 
 
+def measure_vortex_merger(lm, torch, N=128, dt=5e-3, T=25.0):
+    """Sec. 4.1's vortex-merger test at the paper's setup (two-dimensional
+    Euler flow, 128^2, Heun, dt = 0.005, tau = 0, T = 25, inviscid, FP64):
+    zeta~^L against zeta(T) (Eq. vorticity_itsmean) for the pseudospectral
+    Strategy 1 and the semi-Lagrangian one with linear and cubic
+    interpolation (Fig. 3), with the device time of each interval."""
+    n = int(round(T / dt))
+    ic = np.ascontiguousarray(np.stack(si.vortex_pair(N)))
+    res = {"workload": f"{N}^2 vortex pair, Heun, dt {dt}, T {T} ({n} steps), inviscid, FP64", "rel_l2": {},
+           "ms": {}}
+    for name in ("pseudospectral", "linear", "cubic"):
+        h = lm.sw_create(lm.make_params(N, dt, precision="f64", model="euler2d", stepper="heun", nu8=0.0), ic)
+        out = {k: np.zeros((N, N)) for k in ("zeta", "pos_x", "pos_y")}
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if name == "pseudospectral":
+            lm.lmean_begin(h, lm.make_lm_params(1, ("zeta",), pos=True, eulerian=False, n_steps=n))
+            e0.record()
+            lm.lmean_step(h, n)
+            e1.record()
+            lm.lmean_end(h, out)
+        else:
+            s = lm.sw_sl_create(h, lm.make_sl_params(("zeta",), pos=True, scheme="trapezoid", interp=name,
+                                                     n_steps=n))
+            e0.record()
+            lm.sw_sl_step(s, n)
+            e1.record()
+            lm.sw_sl_end(s, out)
+        torch.cuda.synchronize()
+        uvz = np.zeros((3, N, N))
+        lm.sw_get_fields(h, uvz)
+        lm.sw_destroy(h)
+        res["rel_l2"][name] = float(np.linalg.norm(out["zeta"] - uvz[2]) / np.linalg.norm(uvz[2]))
+        res["ms"][name] = e0.elapsed_time(e1)
+    return res
+
+
 def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
     """Poisson stream of Lagrangian-mean requests through sw_server."""
     import time as _t
@@ -628,6 +665,7 @@ def run_ours(args):
         extras["remap"] = measure_remap(lm, torch, outs, list(w.strategies))
         extras["diagnostics"] = measure_diagnostics(lm, torch, outs, list(w.strategies))
         extras["semi_lagrangian"] = measure_semi_lagrangian(lm, torch)
+        extras["vortex_merger"] = measure_vortex_merger(lm, torch)
         extras["batched"] = measure_batched(lm, torch)
         extras["precision_form"] = measure_precision(lm, torch)
         extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)

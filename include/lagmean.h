@@ -64,6 +64,15 @@ extern "C" {
 #define SW_MODEL_KINEMATIC 1 /* test model: the state is passively advected
                                 by the constant velocity (adv_x, adv_y), and
                                 the Lagrangian-mean equations see u = adv   */
+#define SW_MODEL_EULER2D 2   /* two-dimensional incompressible flow, the test
+                                flow of Sec. 4.1: d_t zeta + div(u zeta) = 0
+                                with u = -d_y psi, v = d_x psi, lap psi = zeta.
+                                The third field of an initial condition or of
+                                sw_get_fields is zeta (no depth); the u, v
+                                planes of an initial condition are ignored
+                                (derived from zeta).  Lagrangian means of
+                                zeta, u and v only; sw_diag is SW_EINVAL.
+                                f0, c2 are unused.                            */
 
 /* Lagrangian-mean field mask (lm_params.fields) */
 #define LM_ZETA 1 /* relative vorticity zeta = d_x v - d_y u              */

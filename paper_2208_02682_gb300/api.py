@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "liblagmean.so")
 
 SW_OK, SW_EINVAL, SW_ENOMEM, SW_EBUSY, SW_ERANGE, SW_ESTATE, SW_ETIMEOUT, SW_ECUDA = range(8)
 SW_PREC_FP64, SW_PREC_FP32 = 0, 1
-SW_MODEL_SW, SW_MODEL_KINEMATIC = 0, 1
+SW_MODEL_SW, SW_MODEL_KINEMATIC, SW_MODEL_EULER2D = 0, 1, 2
 LM_ZETA, LM_H, LM_U, LM_V, LM_Q, LM_POS = 1, 2, 4, 8, 16, 32
 FIELD_BITS = {"zeta": LM_ZETA, "h": LM_H, "u": LM_U, "v": LM_V, "q": LM_Q}
 
@@ -181,7 +181,7 @@ def make_params(N, dt, precision="f64", model="sw", f0=1.0, c2=1.0, nu8=0.0, lm_
     p = sw_params()
     p.N = int(N)
     p.precision = {"f64": SW_PREC_FP64, "f32": SW_PREC_FP32}[precision]
-    p.model = {"sw": SW_MODEL_SW, "kinematic": SW_MODEL_KINEMATIC}[model]
+    p.model = {"sw": SW_MODEL_SW, "kinematic": SW_MODEL_KINEMATIC, "euler2d": SW_MODEL_EULER2D}[model]
     p.stepper = {"rk4": 0, "heun": 1, "euler": 2}[stepper]
     p.visc = {"hyper8": 0, "laplace": 1}[visc]
     p.reserved = 0

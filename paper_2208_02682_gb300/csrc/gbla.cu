@@ -238,6 +238,10 @@ extern "C" int sw_sl_create(sw_handle* h, const sl_params* p, sl_interval** out)
     delete s;
     return sl_fail(h, SW_EBUSY, "the handle has an open averaging interval");
   }
+  if (s->hi.model == SW_MODEL_EULER2D && (p->fields & (LM_H | LM_Q))) {
+    delete s;
+    return sl_fail(h, SW_EINVAL, "the two-dimensional Euler model averages zeta, u and v only");
+  }
   while ((1 << s->log2N) < s->hi.N) ++s->log2N;
   const int bits[kMaxSL] = {LM_ZETA, LM_H, LM_U, LM_V, LM_Q};
   const int srcs[kMaxSL] = {SRC_ZETA, SRC_H, SRC_U, SRC_V, SRC_Q};

@@ -368,6 +368,24 @@ __device__ __forceinline__ T bilinear(const T* __restrict__ f, int i, int j, T x
 }
 
 // ---------------------------------------------------------------------------
+// Two-dimensional Euler model: u, v of the vorticity in slot fh, through the
+// streamfunction (u_hat = i ky zeta_hat/|k|^2, v_hat = -i kx zeta_hat/|k|^2,
+// zero at k = 0), into slots fu, fv; one thread per box mode.
+template <typename T>
+__global__ void k_velocity_from_vorticity(cplx<T>* __restrict__ y, Geom g, int fu, int fv, int fh) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ms) return;
+  const int mi = (int)m;
+  const int kyi = mi / g.KXP, kx = mi - kyi * g.KXP;
+  const T kxf = (T)kx, kyf = (T)(kyi - g.K);
+  const cplx<T> z = y[(long long)fh * g.ms + m];
+  const T k2 = kxf * kxf + kyf * kyf;
+  const T inv = k2 > (T)0 ? (T)1 / k2 : (T)0;
+  y[(long long)fu * g.ms + m] = mk<T>(-kyf * z.y * inv, kyf * z.x * inv);
+  y[(long long)fv * g.ms + m] = mk<T>(kxf * z.y * inv, -kxf * z.x * inv);
+}
+
+// ---------------------------------------------------------------------------
 // Spectral FP64 copy of selected fields, value = (y - comp) * scale.
 template <typename T>
 __global__ void k_spec_to_f64(const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ comp,

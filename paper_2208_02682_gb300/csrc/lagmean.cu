@@ -130,7 +130,9 @@ static Layout build_layout(const sw_params& p, int strategy, int fields, int eul
   L.i_u = addi(L.f_u, OP_ID, -1);
   L.i_v = addi(L.f_v, OP_ID, -1);
   L.i_h = addi(L.f_h, OP_ID, -1);
-  L.i_z = addi(L.f_u, OP_CURL, L.f_v);
+  // the two-dimensional Euler model evolves zeta itself (the h slot; its
+  // mean, which a curl of u would drop, included)
+  L.i_z = p.model == SW_MODEL_EULER2D ? L.i_h : addi(L.f_u, OP_CURL, L.f_v);
   // products
   int np = 0;
   auto addp = [&](int kind, int a, int b, int c) {
@@ -146,6 +148,10 @@ static Layout build_layout(const sw_params& p, int strategy, int fields, int eul
     L.p_ke = addp(PK_KE, -1, -1, 0);
     L.p_hu = addp(PK_HU, -1, -1, 0);
     L.p_hv = addp(PK_HV, -1, -1, 0);
+  } else if (p.model == SW_MODEL_EULER2D) {
+    // zeta v and zeta u: d_t zeta = -d_x (u zeta) - d_y (v zeta)
+    L.p_zv = addp(PK_ZV, -1, -1, 0);
+    L.p_zu = addp(PK_ZU, -1, -1, 0);
   }
   if (L.has_q) L.p_q = addp(PK_Q, -1, -1, 0);
   const int ph_of[NLMF] = {PH_Z, PH_H, PH_U, PH_V, PH_Q};
@@ -675,11 +681,17 @@ static int load_ic_from_out64(sw_handle* h) {
   for (int i = 0; i < 3; ++i) cf.src_idx[i] = cf.dst_idx[i] = i;
   CK(h, launch_col_fwd<double>(cf, s));
   // the state holds the depth perturbation eta = h - 1 (mean depth 1 removed
-  // from the k = 0 mode), which keeps its relative precision in FP32
-  CK(h, launch_add_real(h->spec64 + 2 * g.ms + (long long)g.K * g.KXP, -1.0, s));
+  // from the k = 0 mode), which keeps its relative precision in FP32; the
+  // two-dimensional Euler model holds the vorticity there and derives u, v
+  const bool e2 = h->p.model == SW_MODEL_EULER2D;
+  if (!e2) CK(h, launch_add_real(h->spec64 + 2 * g.ms + (long long)g.K * g.KXP, -1.0, s));
   if (h->fp32) CK(h, launch_spec_from_f64<float>(h->spec64, (cplx<float>*)h->y, 3 * g.ms, s));
   else CK(h, launch_spec_from_f64<double>(h->spec64, (cplx<double>*)h->y, 3 * g.ms, s));
-  h->launches += 4;
+  if (e2) {
+    if (h->fp32) CK(h, launch_velocity_from_vorticity<float>((cplx<float>*)h->y, g, h->L.f_u, h->L.f_v, h->L.f_h, s));
+    else CK(h, launch_velocity_from_vorticity<double>((cplx<double>*)h->y, g, h->L.f_u, h->L.f_v, h->L.f_h, s));
+  }
+  h->launches += e2 ? 5 : 4;
   return SW_OK;
 }
 
@@ -697,7 +709,7 @@ static int validate(const sw_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return SW_EINVAL; }
   if (!is_pow2(p->N) || p->N < 16 || p->N > 2048) { why = "N must be a power of two in [16, 2048]"; return SW_EINVAL; }
   if (p->precision != SW_PREC_FP64 && p->precision != SW_PREC_FP32) { why = "precision must be SW_PREC_FP64 or SW_PREC_FP32"; return SW_EINVAL; }
-  if (p->model != SW_MODEL_SW && p->model != SW_MODEL_KINEMATIC) { why = "model must be SW_MODEL_SW or SW_MODEL_KINEMATIC"; return SW_EINVAL; }
+  if (p->model != SW_MODEL_SW && p->model != SW_MODEL_KINEMATIC && p->model != SW_MODEL_EULER2D) { why = "model must be SW_MODEL_SW, SW_MODEL_KINEMATIC or SW_MODEL_EULER2D"; return SW_EINVAL; }
   if (p->reserved != 0) { why = "reserved must be 0"; return SW_EINVAL; }
   if (p->stepper < SW_STEP_RK4 || p->stepper > SW_STEP_EULER) { why = "stepper must be SW_STEP_RK4, SW_STEP_HEUN or SW_STEP_EULER"; return SW_EINVAL; }
   if (p->visc != SW_VISC_HYPER8 && p->visc != SW_VISC_LAPLACE) { why = "visc must be SW_VISC_HYPER8 or SW_VISC_LAPLACE"; return SW_EINVAL; }
@@ -921,6 +933,8 @@ extern "C" int lmean_begin(sw_handle* h, const lm_params* lp) {
     return fail(h, SW_EINVAL, "unknown bits in fields");
   const int scal = lp->fields & (LM_ZETA | LM_H | LM_U | LM_V | LM_Q);
   if (!scal && !(lp->fields & LM_POS)) return fail(h, SW_EINVAL, "no field selected");
+  if (h->p.model == SW_MODEL_EULER2D && (lp->fields & (LM_H | LM_Q)))
+    return fail(h, SW_EINVAL, "the two-dimensional Euler model averages zeta, u and v only");
   if (!scal && lp->eulerian) return fail(h, SW_EINVAL, "Eulerian means need a scalar field");
   Layout L = build_layout(h->p, lp->strategy, lp->fields, lp->eulerian);
   const Geom& g = h->g;
@@ -1017,7 +1031,9 @@ extern "C" int sw_get_fields(sw_handle* h, double* uvh, int on_device) {
   if (!h) return SW_EINVAL;
   h->err.clear();
   if (!uvh) return fail(h, SW_EINVAL, "uvh is NULL");
-  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, 1.0}};
+  // third field: h = 1 + eta (zeta for the two-dimensional Euler model)
+  const double c3 = h->p.model == SW_MODEL_EULER2D ? 0.0 : 1.0;
+  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, c3}};
   // the dynamics fields carry no compensation term (it stays zero)
   int rc = phys_outputs(h, os, 3);
   if (rc) return rc;
@@ -1041,9 +1057,17 @@ extern "C" int sw_set_fields(sw_handle* h, const double* uvh, int on_device) {
 // Physical FP64 u, v, h, zeta of the current state in out64 slots 0..3
 // (zeta by a spectral curl in FP64), on the handle's stream.
 static int phys_uvhz(sw_handle* h) {
-  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0}, {h->L.f_h, 1.0, 0, 0, 2, 1.0}};
+  const bool e2 = h->p.model == SW_MODEL_EULER2D;
+  OutSpec os[3] = {{h->L.f_u, 1.0, 0, 0, 0, 0.0}, {h->L.f_v, 1.0, 0, 0, 1, 0.0},
+                   {h->L.f_h, 1.0, 0, 0, 2, e2 ? 0.0 : 1.0}};
   int rc = phys_outputs(h, os, 3);
   if (rc) return rc;
+  if (e2) {
+    // the evolved vorticity (with its mean) in both the h and the zeta slot
+    CK(h, cudaMemcpyAsync(h->out64 + 3 * h->g.np, h->out64 + 2 * h->g.np, (size_t)h->g.np * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
+    return SW_OK;
+  }
   // zeta = i kx v - i ky u from FP64 copies of u, v
   const Geom& g = h->g;
   if (h->fp32)
@@ -1110,6 +1134,7 @@ extern "C" int sw_diag(sw_handle* h, double out[3]) {
   if (!h) return SW_EINVAL;
   h->err.clear();
   if (!out) return fail(h, SW_EINVAL, "out is NULL");
+  if (h->p.model == SW_MODEL_EULER2D) return fail(h, SW_EINVAL, "sw_diag has no two-dimensional Euler form");
   int rc = phys_uvhz(h);
   if (rc) return rc;
   const Geom& g = h->g;

@@ -61,6 +61,8 @@ template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s);
 template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T>* y, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_velocity_from_vorticity(cplx<T>* y, const Geom& g, int fu, int fv, int fh, cudaStream_t s);
 cudaError_t launch_diag(const double* phys, long long np, double f0, double c2, double* part, int nblk,
                         double* out, cudaStream_t s);
 cudaError_t launch_add_real(double2* p, double delta, cudaStream_t s);
@@ -173,6 +175,12 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_velocity_from_vorticity(cplx<T>* y, const Geom& g, int fu, int fv, int fh, cudaStream_t s) {
+  k_velocity_from_vorticity<T><<<(unsigned)((g.ms + 255) / 256), 256, 0, s>>>(y, g, fu, fv, fh);
+  return cudaGetLastError();
+}
+
 #define LM_INSTANTIATE_ALL(T)                                                                               \
   template cudaError_t launch_col_inv<T>(const ColInvArgs<T>&, cudaStream_t);                               \
   template cudaError_t launch_col_fwd<T>(const ColFwdArgs<T>&, cudaStream_t);                               \
@@ -182,7 +190,8 @@ template <typename T> cudaError_t launch_spec_from_f64(const double2* in, cplx<T
                                        bool, cudaStream_t);                                                 \
   template cudaError_t launch_spec_to_f64<T>(const cplx<T>*, const cplx<T>*, double2*, long long, int, int,  \
                                              double, cudaStream_t);                                         \
-  template cudaError_t launch_spec_from_f64<T>(const double2*, cplx<T>*, long long, cudaStream_t);
+  template cudaError_t launch_spec_from_f64<T>(const double2*, cplx<T>*, long long, cudaStream_t);            \
+  template cudaError_t launch_velocity_from_vorticity<T>(cplx<T>*, const Geom&, int, int, int, cudaStream_t);
 #endif
 
 }  // namespace lm

@@ -451,6 +451,19 @@ __device__ __forceinline__ double kahan_add_rn(double sum, double add, double& c
   return t;
 }
 
+// Two-dimensional Euler model: the velocity of the vorticity zeta in buffer b
+// at mode m, through the streamfunction (lap psi = zeta, u = -d_y psi,
+// v = d_x psi): u_hat = i ky zeta_hat/|k|^2, v_hat = -i kx zeta_hat/|k|^2, zero
+// at k = 0; written beside zeta.
+template <typename T>
+__device__ __forceinline__ void slave_velocity(cplx<T>* b, const Layout& L, long long ms, long long m, T kxf, T kyf) {
+  const cplx<T> z = b[L.f_h * ms + m];
+  const T k2 = kxf * kxf + kyf * kyf;
+  const T inv = k2 > (T)0 ? (T)1 / k2 : (T)0;
+  b[L.f_u * ms + m] = mk<T>(-kyf * z.y * inv, kyf * z.x * inv);
+  b[L.f_v * ms + m] = mk<T>(kxf * z.y * inv, -kxf * z.x * inv);
+}
+
 // y_{n+1} = E^2 y_n + inc at element o of field f (compensated in FP32 for
 // the fields marked so).
 template <typename T>
@@ -479,23 +492,30 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int st = d.c.stepper;
+  const int role = L.frole[f], slot = L.fslot[f];
+  // two-dimensional Euler model: u and v follow zeta (written with it)
+  const bool e2 = L.model == 2;
+  if (e2 && (role == R_U || role == R_V)) return;
   const int cls = L.fclass[f];
   const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
   const long long o = f * g.ms + m;
+  const T kxf = (T)kx, kyf = (T)(kyi - g.K);
   if (st == 2 && stage == 1) {
     // forward Euler, second pass: y_{n+1} = E^2 y_n + dt E^2 a, the increment
     // from the first pass (a separate pass: the first reads other fields' y_n)
     commit_mode<T>(d, f, o, E, d.acc[o]);
+    if (e2 && role == R_H) slave_velocity<T>(d.y, L, g.ms, m, kxf, kyf);
     return;
   }
-  const T kxf = (T)kx, kyf = (T)(kyi - g.K);
   const T dt = d.cdt;
   const cplx<T>* yin = stage_input(d, stage);
-  const int role = L.frole[f], slot = L.fslot[f];
   cplx<T> rhs;
   if (role <= R_H) {
     // shallow-water right-hand side, Eq. (sw_eqs_dimless)
-    if (L.model == 0) {
+    if (e2) {
+      // vorticity of the two-dimensional Euler flow: d_t zeta = -div(u zeta)
+      rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(prod(L.p_zu), kxf), cik<T>(prod(L.p_zv), kyf)));
+    } else if (L.model == 0) {
       if (role == R_H) {
         rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(prod(L.p_hu), kxf), cik<T>(prod(L.p_hv), kyf)));
       } else {
@@ -529,7 +549,9 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
     // f_hat of the averaged scalar at this stage
     const int sc = L.lmf[slot];
     cplx<T> fh;
-    if (sc == LMF_ZETA) fh = csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
+    if (sc == LMF_ZETA)
+      fh = e2 ? yin[L.f_h * g.ms + m]  // the evolved vorticity (its mean included)
+              : csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
     else if (sc == LMF_H) fh = yin[L.f_h * g.ms + m];
     else if (sc == LMF_U) fh = yin[L.f_u * g.ms + m];
     else if (sc == LMF_V) fh = yin[L.f_v * g.ms + m];
@@ -566,6 +588,7 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
     // or dt/2 (acc + b) (Heun); its inputs are the stage buffers, not y
     commit_mode<T>(d, f, o, E, cscale<T>(cadd<T>(d.acc[o], rhs), st == 0 ? dt / (T)6 : dt / (T)2));
   }
+  if (e2 && role == R_H && st != 2) slave_velocity<T>(last ? d.y : yout, L, g.ms, m, kxf, kyf);
 }
 
 // Modes per block of the update kernel (two per thread: the grid of a
