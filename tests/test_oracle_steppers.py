@@ -90,3 +90,24 @@ def test_viscosity_placement_on_depth(visc):
     damp = 1.0 if visc == "laplace" else math.exp(-nu * k2 ** 4 * dt * n)
     assert abs(o.hh[ky, kx] - e0 * damp) < 1e-14
     assert np.abs(o.uh).max() < 1e-300 and np.abs(o.vh).max() < 1e-300
+
+
+def test_paper_setup_initial_condition():
+    # Sec. 4.2.1: f0 = 1/Ro = 10, c2 = 1/Fr^2 = 4, omega = 10.2; the stand-in
+    # turbulence (the initial condition minus the Eq. (initial_wave) wave) has
+    # the requested rms velocity and is in geostrophic balance,
+    # f0 z x u = -c2 grad eta
+    N = 64
+    (u, v, h), p = si.paper_sw_setup(N)
+    assert p["f0"] == 10.0 and p["c2"] == 4.0 and p["n_steps"] == 17600
+    assert abs(si.wave_frequency(1.0, p["f0"], p["c2"]) - 10.2) < 5e-3
+    uw, vw, hw = si.mode1_wave(N, -1.8, p["f0"], p["c2"])
+    ub, vb, eb = u - uw, v - vw, h - hw
+    assert abs(np.sqrt(np.mean(ub * ub + vb * vb)) - 0.3) < 1e-12
+    k = np.fft.fftfreq(N, 1.0 / N)
+    KX, KY = np.meshgrid(k, k)
+    ex = np.real(np.fft.ifft2(1j * KX * np.fft.fft2(eb)))
+    ey = np.real(np.fft.ifft2(1j * KY * np.fft.fft2(eb)))
+    np.testing.assert_allclose(-p["f0"] * vb, -p["c2"] * ex, atol=1e-12)
+    np.testing.assert_allclose(p["f0"] * ub, -p["c2"] * ey, atol=1e-12)
+    assert h.min() > 0.2
