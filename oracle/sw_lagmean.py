@@ -161,13 +161,23 @@ class SWOracle:
 
     # -- interval bookkeeping ---------------------------------------------
     def lmean_begin(self, strategy, fields=("zeta", "h", "u", "v"), pos=True,
-                    eulerian=True, n_steps=1):
+                    eulerian=True, n_steps=1, scheme="coupled"):
         """Open an averaging interval at tau = current time (Sec. 2: each
         interval [tau_n, tau_n + T] is computed independently).  Initial
         conditions g = D = 0 (Strategy 1, g = (t - tau) f~ at t = tau) and
-        xi = g = 0 (Strategy 2, Xi(x, tau) = x)."""
+        xi = g = 0 (Strategy 2, Xi(x, tau) = x).
+
+        scheme "coupled": the mean fields share the dynamics' stages.
+        scheme "xi_first": the paper's discretisation of Eqs. (xi_evol),
+        (barf_xi) in Sec. 4.2 / 4.2.1 (Strategy 2, forward Euler): the mean
+        equations step by 2 dt every other dynamics step, xi first, then gbar
+        with the updated xi (see _euler_step)."""
         if strategy not in (1, 2):
             raise ValueError("strategy must be 1 or 2")
+        if scheme not in ("coupled", "xi_first"):
+            raise ValueError(scheme)
+        if scheme == "xi_first" and (strategy != 2 or self.stepper != "euler" or int(n_steps) % 2):
+            raise ValueError("xi_first needs Strategy 2, forward Euler and an even n_steps")
         fields = tuple(f for f in LM_FIELDS if f in fields)
         if self.model == "euler2d" and ("h" in fields or "q" in fields):
             raise ValueError("euler2d averages zeta, u and v only")
@@ -175,7 +185,7 @@ class SWOracle:
             pos = True  # xi is part of the Strategy-2 dynamics
         z = lambda: np.zeros_like(self.uh)
         self.lm = dict(strategy=strategy, fields=fields, pos=bool(pos),
-                       eulerian=bool(eulerian), n_steps=int(n_steps), done=0,
+                       eulerian=bool(eulerian), n_steps=int(n_steps), done=0, scheme=scheme,
                        G={f: z() for f in fields},
                        P=[z(), z()] if pos else None,
                        E={f: z() for f in fields} if eulerian else None)
@@ -261,6 +271,9 @@ class SWOracle:
             wgx = wx * self.phys(self.dx(Xx)) + wy * self.phys(self.dy(Xx))
             wgy = wx * self.phys(self.dx(Xy)) + wy * self.phys(self.dy(Xy))
             out["P"] = [self.spec(uI - wx - wgx), self.spec(vI - wy - wgy)]
+            if lm["scheme"] == "xi_first":
+                # gbar steps with the updated xi, at its own time s + dt
+                wx, wy = xi_x / (s + self.dt), xi_y / (s + self.dt)
             out["G"] = {}
             for f in lm["fields"]:
                 G = st["G"][f]
@@ -328,12 +341,31 @@ class SWOracle:
 
     def _euler_step(self, s0):
         """Forward Euler (the paper's stepper in Sec. 4.2.1) with the
-        integrating factor: y_{n+1} = E^2 (y_n + dt N(y_n))."""
+        integrating factor: y_{n+1} = E^2 (y_n + dt N(y_n)).
+
+        With the "xi_first" scheme (Sec. 4.2: xi is updated first and the
+        updated xi used for gbar; Sec. 4.2.1: the mean equations' step is
+        twice the dynamics' step), step 2m advances xi by 2 dt from the flow
+        at t_2m, xi_{m+1} = E^4 (xi_m + 2 dt R_xi(xi_m, t_2m)), and step
+        2m + 1 advances gbar with the updated xi at its time s_{m+1} = (2m +
+        2) dt and the flow at t_2m+1, gbar_{m+1} = E^4 (gbar_m + 2 dt
+        R_g(gbar_m, xi_{m+1})); the Eulerian accumulators step with dt.
+        The time level of gbar's advecting velocity xi_{m+1}/s_{m+1} is a
+        reading (the paper does not state it) that no pin distinguishes:
+        other consistent choices converge at the same first order."""
         dt = self.dt
         y = self._state()
         E = self._efac_tree(y, self._factors())
         a = self._rhs(y, s0)
-        self._commit(self._map(lambda yy, aa, e: e * e * (yy + dt * aa), y, a, E))
+        yn = self._map(lambda yy, aa, e: e * e * (yy + dt * aa), y, a, E)
+        lm = self.lm
+        if lm is not None and lm["scheme"] == "xi_first":
+            step2 = lambda yy, aa, e: (e * e) * (e * e) * (yy + 2.0 * dt * aa)
+            keep = lambda yy, aa, e: yy
+            even = lm["done"] % 2 == 0
+            yn["P"] = self._map(step2 if even else keep, y["P"], a["P"], E["P"])
+            yn["G"] = self._map(keep if even else step2, y["G"], a["G"], E["G"])
+        self._commit(yn)
 
     def _commit(self, yn):
         self.uh, self.vh, self.hh = yn["sw"]

@@ -111,3 +111,57 @@ def test_paper_setup_initial_condition():
     np.testing.assert_allclose(-p["f0"] * vb, -p["c2"] * ex, atol=1e-12)
     np.testing.assert_allclose(p["f0"] * ub, -p["c2"] * ey, atol=1e-12)
     assert h.min() > 0.2
+
+
+def test_xi_first_uniform_flow_exact():
+    # Sec. 4.2's xi-first discretisation with the mean equations stepping by
+    # 2 dt: in a uniform flow (f0 = 0) the partial mean displacement is
+    # xi = U s/2 and the mean of u is U exactly, at every completed mean step
+    N, dt, U0, V0, n = 16, 5e-3, 0.7, -0.3, 40
+    u, v, h = si.uniform_flow(N, U0, V0)
+    o = SWOracle(N, dt, u, v, h, f0=0.0, stepper="euler")
+    o.lmean_begin(2, fields=("u", "v"), pos=True, eulerian=False, n_steps=n, scheme="xi_first")
+    o.lmean_step(n)
+    r = o.lmean_end()
+    T = n * dt
+    x = 2 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    np.testing.assert_allclose(r["pos_x"] - X, U0 * T / 2, atol=1e-14)
+    np.testing.assert_allclose(r["pos_y"] - Y, V0 * T / 2, atol=1e-14)
+    np.testing.assert_allclose(r["u"], U0, atol=1e-14)
+    np.testing.assert_allclose(r["v"], V0, atol=1e-14)
+
+
+def _run_xi_first(dt, T=0.4, N=32):
+    u, v, h = si.smooth_flow(N, 2, seed=8, uamp=0.15, eamp=0.05)
+    n = int(round(T / dt))
+    o = SWOracle(N, dt, u, v, h, nu8=0.0, stepper="euler")
+    o.lmean_begin(2, fields=("zeta", "u"), pos=True, eulerian=False, n_steps=n, scheme="xi_first")
+    o.lmean_step(n)
+    return o.lmean_end()
+
+
+def test_xi_first_first_order_against_a_fine_reference():
+    u, v, h = si.smooth_flow(32, 2, seed=8, uamp=0.15, eamp=0.05)
+    o = SWOracle(32, 1e-3 / 4, u, v, h, nu8=0.0)
+    n = int(round(0.4 / (1e-3 / 4)))
+    o.lmean_begin(2, fields=("zeta", "u"), pos=True, eulerian=False, n_steps=n)
+    o.lmean_step(n)
+    ref = o.lmean_end()
+    errs = []
+    for dt in (4e-3, 2e-3):
+        out = _run_xi_first(dt)
+        errs.append(max(rel_l2(out["zeta"], ref["zeta"]), rel_l2(out["u"], ref["u"]),
+                        np.abs(out["pos_x"] - ref["pos_x"]).max()))
+    ratio = errs[0] / errs[1]
+    assert 2 * 0.8 < ratio < 2 * 1.25, (errs, ratio)
+
+
+def test_xi_first_needs_strategy2_euler_and_even_steps():
+    u, v, h = si.smooth_flow(16, 2, seed=1)
+    with pytest.raises(ValueError):
+        SWOracle(16, 1e-3, u, v, h, stepper="euler").lmean_begin(1, n_steps=4, scheme="xi_first")
+    with pytest.raises(ValueError):
+        SWOracle(16, 1e-3, u, v, h, stepper="heun").lmean_begin(2, n_steps=4, scheme="xi_first")
+    with pytest.raises(ValueError):
+        SWOracle(16, 1e-3, u, v, h, stepper="euler").lmean_begin(2, n_steps=5, scheme="xi_first")
