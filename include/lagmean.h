@@ -119,12 +119,27 @@ typedef struct sw_params {
   int32_t reserved;  /* must be 0                                           */
 } sw_params;
 
+/* Discretisation of the mean equations (lm_params.scheme):
+ *   LM_SCHEME_COUPLED   the mean fields share every stage of the dynamics'
+ *                       stepper (the default);
+ *   LM_SCHEME_XI_FIRST  the paper's scheme for Strategy 2 (Sec. 4.2: xi is
+ *                       updated first and the updated xi is used for gbar;
+ *                       Sec. 4.2.1: forward Euler, the mean equations'
+ *                       step twice the dynamics' step): step 2m advances xi
+ *                       by 2 dt from the flow at t_2m, step 2m+1 advances
+ *                       gbar by 2 dt with xi_{m+1} (advecting velocity
+ *                       xi_{m+1}/s_{m+1}) and the flow at t_2m+1; Eulerian
+ *                       means step with dt.  Needs strategy 2,
+ *                       SW_STEP_EULER and an even n_steps (else SW_EINVAL). */
+#define LM_SCHEME_COUPLED 0
+#define LM_SCHEME_XI_FIRST 1
+
 /* One averaging interval (lmean_begin). */
 typedef struct lm_params {
   int32_t strategy; /* 1 or 2                                               */
   int32_t fields;   /* LM_* mask; at least one of ZETA,H,U,V,Q or POS       */
   int32_t eulerian; /* nonzero: also accumulate Eulerian means of `fields`   */
-  int32_t reserved; /* must be 0                                            */
+  int32_t scheme;   /* LM_SCHEME_COUPLED (0) or LM_SCHEME_XI_FIRST            */
   int64_t n_steps;  /* interval length T = n_steps * dt, >= 1               */
 } lm_params;
 

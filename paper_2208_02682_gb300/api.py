@@ -45,7 +45,7 @@ class sw_params(C.Structure):
 
 class lm_params(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("fields", C.c_int32), ("eulerian", C.c_int32),
-                ("reserved", C.c_int32), ("n_steps", C.c_int64)]
+                ("scheme", C.c_int32), ("n_steps", C.c_int64)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -192,7 +192,7 @@ def make_params(N, dt, precision="f64", model="sw", f0=1.0, c2=1.0, nu8=0.0, lm_
 
 
 def make_lm_params(strategy, fields=("zeta", "h", "u", "v"), pos=True, eulerian=True,
-                   n_steps=1) -> lm_params:
+                   n_steps=1, scheme="coupled") -> lm_params:
     lp = lm_params()
     lp.strategy = int(strategy)
     bits = 0
@@ -202,7 +202,7 @@ def make_lm_params(strategy, fields=("zeta", "h", "u", "v"), pos=True, eulerian=
         bits |= LM_POS
     lp.fields = bits
     lp.eulerian = 1 if eulerian else 0
-    lp.reserved = 0
+    lp.scheme = {"coupled": 0, "xi_first": 1}[scheme]
     lp.n_steps = int(n_steps)
     return lp
 

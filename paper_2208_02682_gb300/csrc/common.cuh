@@ -100,6 +100,7 @@ enum { R_U = 0, R_V = 1, R_H = 2, R_G = 3, R_P = 4, R_E = 5 };
 
 struct Layout {
   int strategy;   // 0: dynamics only, 1 or 2
+  int scheme;     // SCHEME_* (the C ABI's LM_SCHEME_*) of the open interval
   int model;      // 0 shallow water, 1 kinematic
   int nf;         // evolved spectral fields
   int ni;         // mixed intermediates produced by the column pass
@@ -127,6 +128,9 @@ struct Layout {
   int p_g[NLMF];
   int p_p[2];
 };
+
+// discretisation of the mean equations (the C ABI's LM_SCHEME_* values)
+enum { SCHEME_COUPLED = 0, SCHEME_XI_FIRST = 1 };
 
 struct StepConsts {
   double dt, f0, c2, adv_x, adv_y;

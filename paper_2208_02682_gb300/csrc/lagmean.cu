@@ -78,10 +78,13 @@ static int fail_cuda(sw_handle* h, const char* what, cudaError_t e) {
 
 // ---------------------------------------------------------------------------
 // Field layout of a configuration.
-static Layout build_layout(const sw_params& p, int strategy, int fields, int eulerian) {
+static_assert(SCHEME_COUPLED == LM_SCHEME_COUPLED && SCHEME_XI_FIRST == LM_SCHEME_XI_FIRST, "scheme values");
+
+static Layout build_layout(const sw_params& p, int strategy, int fields, int eulerian, int scheme = 0) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   L.strategy = strategy;
+  L.scheme = scheme;
   L.model = p.model;
   L.p_zv = L.p_zu = L.p_ke = L.p_hu = L.p_hv = L.p_q = -1;
   for (int j = 0; j < NLMF; ++j) L.f_g[j] = L.f_e[j] = L.p_g[j] = -1;
@@ -927,7 +930,11 @@ extern "C" int lmean_begin(sw_handle* h, const lm_params* lp) {
   if (!lp) return fail(h, SW_EINVAL, "lm_params is NULL");
   if (h->lm_open) return fail(h, SW_ESTATE, "an averaging interval is already open");
   if (lp->strategy != 1 && lp->strategy != 2) return fail(h, SW_EINVAL, "strategy must be 1 or 2");
-  if (lp->reserved != 0) return fail(h, SW_EINVAL, "reserved must be 0");
+  if (lp->scheme != LM_SCHEME_COUPLED && lp->scheme != LM_SCHEME_XI_FIRST)
+    return fail(h, SW_EINVAL, "scheme must be LM_SCHEME_COUPLED or LM_SCHEME_XI_FIRST");
+  if (lp->scheme == LM_SCHEME_XI_FIRST &&
+      (lp->strategy != 2 || h->p.stepper != SW_STEP_EULER || (lp->n_steps & 1)))
+    return fail(h, SW_EINVAL, "LM_SCHEME_XI_FIRST needs strategy 2, SW_STEP_EULER and an even n_steps");
   if (lp->n_steps < 1) return fail(h, SW_EINVAL, "n_steps must be >= 1");
   if (lp->fields & ~(LM_ZETA | LM_H | LM_U | LM_V | LM_Q | LM_POS))
     return fail(h, SW_EINVAL, "unknown bits in fields");
@@ -936,7 +943,7 @@ extern "C" int lmean_begin(sw_handle* h, const lm_params* lp) {
   if (h->p.model == SW_MODEL_EULER2D && (lp->fields & (LM_H | LM_Q)))
     return fail(h, SW_EINVAL, "the two-dimensional Euler model averages zeta, u and v only");
   if (!scal && lp->eulerian) return fail(h, SW_EINVAL, "Eulerian means need a scalar field");
-  Layout L = build_layout(h->p, lp->strategy, lp->fields, lp->eulerian);
+  Layout L = build_layout(h->p, lp->strategy, lp->fields, lp->eulerian, lp->scheme);
   const Geom& g = h->g;
   const size_t cs = 2 * h->tsz;
   // zero the mean fields, their compensation terms and the step counter
@@ -1216,7 +1223,7 @@ extern "C" int sw_set_state(sw_handle* h, const void* blob, size_t size) {
       hd.f0 != h->p.f0 || hd.c2 != h->p.c2 || hd.nu8 != h->p.nu8 || hd.lm_nu8 != h->p.lm_nu8 ||
       hd.adv_x != h->p.adv_x || hd.adv_y != h->p.adv_y || hd.stepper != h->p.stepper || hd.visc != h->p.visc)
     return fail(h, SW_EINVAL, "blob parameters differ from the handle's");
-  Layout L = hd.lm_open ? build_layout(h->p, hd.lp.strategy, hd.lp.fields, hd.lp.eulerian)
+  Layout L = hd.lm_open ? build_layout(h->p, hd.lp.strategy, hd.lp.fields, hd.lp.eulerian, hd.lp.scheme)
                         : build_layout(h->p, 0, 0, 0);
   if (L.nf != hd.nf || size < blob_size(h, hd.nf)) return fail(h, SW_EINVAL, "blob size mismatch");
   const size_t fb = (size_t)hd.nf * h->g.ms * 2 * h->tsz;

@@ -283,6 +283,9 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const T s = stage_time<T>(d.ctr, stage, d.cdt, d.c.stepper);
   const bool s0 = !(s > (T)0);
   const T inv_s = s0 ? (T)0 : (T)1 / s;
+  // xi-first scheme: gbar steps with the updated xi at its time s + dt
+  const bool xf = L.scheme == SCHEME_XI_FIRST;
+  const T inv_sg = xf ? (T)1 / (s + d.cdt) : inv_s;
   const T inv_dx = (T)N / (T)6.283185307179586476925286766559;
   const cplx<T>* mix = d.mix;
   // the gather buffer (written by the previous kernel) is read-only here:
@@ -408,8 +411,10 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
             const int e = m * G + j;
             const T xx = XI[e], xy = XI[N + e];
             const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
-            const T wx = s0 ? (T)0.5 * ua : xx * inv_s;
-            const T wy = s0 ? (T)0.5 * va : xy * inv_s;
+            const bool sz = s0 && !(xf && kind == PK_GBAR);
+            const T is = kind == PK_GBAR ? inv_sg : inv_s;
+            const T wx = sz ? (T)0.5 * ua : xx * is;
+            const T wy = sz ? (T)0.5 * va : xy * is;
             const T wgrad = wx * x[m].x + wy * x[m].y;
             const T fi = (kind == PK_XI && kin) ? (pc == 0 ? adv_x : adv_y) : sv[e];
             put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wgrad : fi - wgrad);
@@ -487,8 +492,8 @@ __device__ __forceinline__ void commit_mode(const RunDesc<T>& d, int f, long lon
 // Right-hand side and RK4 update of evolved field f at mode m = kyi*KXP + kx
 // (kx <= K); prod(p) returns the spectral product p at this mode.
 template <typename T, typename PF>
-__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd, int f, long long m, int kx,
-                                            int kyi, PF prod) {
+__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd, bool even, int f, long long m,
+                                            int kx, int kyi, PF prod) {
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int st = d.c.stepper;
@@ -500,10 +505,15 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
   const long long o = f * g.ms + m;
   const T kxf = (T)kx, kyf = (T)(kyi - g.K);
+  // xi-first scheme (Strategy 2, forward Euler): xi steps by 2 dt on even
+  // steps, gbar on odd ones (integrating factor over 2 dt: E^4)
+  const bool x1 = L.scheme == SCHEME_XI_FIRST && (role == R_P || role == R_G);
+  const bool active = !x1 || ((role == R_P) == even);
+  if (!active) return;
   if (st == 2 && stage == 1) {
     // forward Euler, second pass: y_{n+1} = E^2 y_n + dt E^2 a, the increment
     // from the first pass (a separate pass: the first reads other fields' y_n)
-    commit_mode<T>(d, f, o, E, d.acc[o]);
+    commit_mode<T>(d, f, o, x1 ? E * E : E, d.acc[o]);
     if (e2 && role == R_H) slave_velocity<T>(d.y, L, g.ms, m, kxf, kyf);
     return;
   }
@@ -568,8 +578,9 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   cplx<T>* yout = stage == 1 ? d.ysb : d.ysa;
   const bool last = stage == stage_count(st) - 1;
   if (st == 2) {
-    // forward Euler, first pass: the increment dt E^2 a
-    d.acc[o] = cscale<T>(rhs, dt * E * E);
+    // forward Euler, first pass: the increment dt E^2 a (xi-first mean
+    // fields: 2 dt E^4 a)
+    d.acc[o] = cscale<T>(rhs, x1 ? (T)2 * dt * (E * E) * (E * E) : dt * E * E);
   } else if (!last && st != 0) {
     // Heun, stage 0: acc = E^2 a, y1 = E^2 (y_n + dt a)
     d.acc[o] = cscale<T>(rhs, E * E);
@@ -592,11 +603,13 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
 }
 
 // Modes per block of the update kernel (two per thread: the grid of a
-// 256^2 Strategy-1 + Strategy-2 batch then fits in one wave of blocks).
+// 256^2 Strategy-1 + Strategy-2 batch then fits in one wave of blocks, with
+// six resident blocks per SM in FP32, i.e. at most 40 registers).
 constexpr int UPD_MODES = 512;
+template <typename T> constexpr int update_min_blocks() { return sizeof(T) == 4 ? 6 : 4; }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restrict__ runs,
+__global__ void __launch_bounds__(256, update_min_blocks<T>()) k_stage_update(const RunDesc<T>* __restrict__ runs,
                                                       const int* __restrict__ start, int nruns, int stage) {
   const int r = find_run(start, nruns, blockIdx.x);
   LM_STAGE_DESC(T);  // many field lookups per thread: read from shared memory
@@ -608,6 +621,7 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
   const int f = lb / mblocks;
   const long long m0 = (long long)(lb - f * mblocks) * UPD_MODES + threadIdx.x;
   const T sd = stage_time<T>(d.ctr, stage, d.cdt, d.c.stepper);
+  const bool even = L.scheme == SCHEME_XI_FIRST ? ((*d.ctr & 1LL) == 0) : true;
 #pragma unroll
   for (int u = 0; u < UPD_MODES / 256; ++u) {
     const long long m = m0 + u * 256;
@@ -617,7 +631,7 @@ __global__ void __launch_bounds__(256) k_stage_update(const RunDesc<T>* __restri
       const int mi = (int)m;
       const int kyi = mi / g.KXP, kx = mi - kyi * g.KXP;
       if (kx <= g.K) {
-        update_mode<T>(d, stage, sd, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
+        update_mode<T>(d, stage, sd, even, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
       }
     }
   }

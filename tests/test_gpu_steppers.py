@@ -190,3 +190,64 @@ def test_repeated_runs_are_bitwise_equal(lm, stepper):
     for o in outs[1:]:
         for k in o:
             assert np.array_equal(o[k], outs[0][k]), k
+
+
+@pytest.mark.parametrize("N", [32, 64])
+@pytest.mark.parametrize("fields", [("zeta", "h", "u", "v"), ("q",)])
+def test_xi_first_matches_oracle_fp64(lm, N, fields):
+    # the paper's Strategy-2 discretisation (Sec. 4.2, 4.2.1); the interval
+    # is stepped in chunks that split a mean step (odd boundary)
+    n, dt = 24, 5e-3
+    uvh = si.smooth_flow(N, 2, seed=11, uamp=0.15, eamp=0.05)
+    nu = _nu("hyper8", N)
+    p = lm.make_params(N, dt, precision="f64", nu8=nu, stepper="euler")
+    h = lm.sw_create(p, np.ascontiguousarray(np.stack(uvh)))
+    try:
+        lm.lmean_begin(h, lm.make_lm_params(2, fields, pos=True, eulerian=True, n_steps=n, scheme="xi_first"))
+        lm.lmean_step(h, 7)
+        lm.lmean_step(h, n - 7)
+        keys = list(fields) + ["pos_x", "pos_y"] + ["e_" + f for f in fields]
+        g = {k: np.zeros((N, N)) for k in keys}
+        lm.lmean_end(h, g)
+    finally:
+        lm.sw_destroy(h)
+    o = SWOracle(N, dt, *uvh, nu8=nu, stepper="euler")
+    o.lmean_begin(2, fields=fields, pos=True, eulerian=True, n_steps=n, scheme="xi_first")
+    o.lmean_step(n)
+    r = oracle_keys(o.lmean_end())
+    errs = compare(g, r, N, 2)
+    assert max(errs.values()) < TOL64, errs
+
+
+def test_xi_first_uniform_flow_closed_form(lm):
+    N, dt, U0, V0, n = 16, 5e-3, 0.7, -0.3, 40
+    u, v, h0 = si.uniform_flow(N, U0, V0)
+    h = lm.sw_create(lm.make_params(N, dt, precision="f64", f0=0.0, stepper="euler"),
+                     np.ascontiguousarray(np.stack([u, v, h0])))
+    try:
+        lm.lmean_begin(h, lm.make_lm_params(2, ("u", "v"), pos=True, eulerian=False, n_steps=n, scheme="xi_first"))
+        lm.lmean_step(h, n)
+        out = {k: np.zeros((N, N)) for k in ("u", "v", "pos_x", "pos_y")}
+        lm.lmean_end(h, out)
+    finally:
+        lm.sw_destroy(h)
+    T = n * dt
+    x = 2 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    np.testing.assert_allclose(out["pos_x"] - X, U0 * T / 2, atol=1e-13)
+    np.testing.assert_allclose(out["pos_y"] - Y, V0 * T / 2, atol=1e-13)
+    np.testing.assert_allclose(out["u"], U0, atol=1e-13)
+    np.testing.assert_allclose(out["v"], V0, atol=1e-13)
+
+
+def test_xi_first_error_codes(lm):
+    N = 32
+    uvh = np.ascontiguousarray(np.stack(si.smooth_flow(N, 2, seed=3)))
+    for stepper, strategy, n in (("euler", 1, 4), ("rk4", 2, 4), ("euler", 2, 5)):
+        h = lm.sw_create(lm.make_params(N, 5e-3, precision="f64", stepper=stepper), uvh)
+        try:
+            with pytest.raises(lm.SWError) as ei:
+                lm.lmean_begin(h, lm.make_lm_params(strategy, ("u",), n_steps=n, scheme="xi_first"))
+            assert ei.value.code == lm.api.SW_EINVAL
+        finally:
+            lm.sw_destroy(h)
