@@ -91,3 +91,21 @@ def test_rejects_depth_and_pv_means():
         o.lmean_begin(1, fields=("zeta", "h"), n_steps=2)
     with pytest.raises(ValueError):
         o.lmean_begin(2, fields=("q",), n_steps=2)
+
+
+def test_fig3_ordering_of_the_three_discretisations():
+    # Fig. 3 (Sec. 4.1, App. B): for the materially conserved vorticity the
+    # pseudospectral zeta~^L is closest to zeta(T), the semi-Lagrangian one
+    # with cubic interpolation next, with linear interpolation last
+    from oracle.gbla import SLInterval
+    N, dt, n = 32, 1e-2, 300
+    o = SWOracle(N, dt, *si.vortex_pair(N), model="euler2d", stepper="heun")
+    o.lmean_begin(1, fields=("zeta",), pos=True, eulerian=False, n_steps=n)
+    o.lmean_step(n)
+    err = {"pseudospectral": rel_l2(o.lmean_end()["zeta"], o.fields()[2])}
+    for interp in ("linear", "cubic"):
+        sl = SLInterval(SWOracle(N, dt, *si.vortex_pair(N), model="euler2d", stepper="heun"), fields=("zeta",),
+                        scheme="trapezoid", interp=interp, n_steps=n)
+        sl.step(n)
+        err[interp] = rel_l2(sl.end()["zeta"], sl.o.fields()[2])
+    assert err["pseudospectral"] < 1e-4 < err["cubic"] < err["linear"], err
