@@ -32,6 +32,16 @@ PLANTS = [
      "tests/test_oracle_gbla.py::test_one_cell_per_step_matches_characteristic_sums"),
     ("remap.py", "return fbar, X + xi_x, Y + xi_y, resid", "return fbar, X - xi_x, Y - xi_y, resid",
      "tests/test_oracle_remap.py::test_whole_cell_shift_is_an_exact_roll"),
+    ("sw_lagmean.py", "yn = m(lambda yy, aa, bb, e: e * e * yy + (dt / 2.0) * (e * e * aa + bb), y, a, b, E)",
+     "yn = m(lambda yy, aa, bb, e: e * e * yy + (dt / 2.0) * (aa + bb), y, a, b, E)",
+     "tests/test_oracle_steppers.py::test_laplacian_integrating_factor_exact"),
+    ("sw_lagmean.py", "e_h = np.ones_like(k8) if self.visc_p == 1 else e_sw", "e_h = e_sw",
+     "tests/test_oracle_steppers.py::test_viscosity_placement_on_depth"),
+    ("remap.py", "return {k: bilinear_at_displacement(v, pos_x - X, pos_y - Y) for k, v in fields.items()}",
+     "return {k: bilinear_at_displacement(v, X - pos_x, Y - pos_y) for k, v in fields.items()}",
+     "tests/test_oracle_diagnostics.py::test_lift_exact_cases"),
+    ("remap.py", "np.add.at(out, sh[box], 0.5 * np.abs(F[box]) ** 2)", "np.add.at(out, sh[box], np.abs(F[box]) ** 2)",
+     "tests/test_oracle_diagnostics.py::test_spectrum_single_modes_and_box"),
 ]
 
 
