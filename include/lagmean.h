@@ -158,6 +158,10 @@ typedef struct lm_result {
 } lm_result;
 
 /* Create a handle from a physical initial condition.
+ * The state is the shallow-water system of Sec. 4.2, Eq. (sw_eqs_dimless)
+ * (momentum Eq. (sw_momentum_dimless), mass Eq. (sw_mass_dimless)), in the
+ * paper's pseudospectral discretisation with 2/3 dealiasing (Sec. 4.1,
+ * 4.2.1): the state is the truncated spectrum of u, v and the depth.
  * ic_uvh: 3*N*N doubles (u, then v, then h), host memory if ic_on_device == 0
  * else device memory; copied, not retained.  The fields are transformed and
  * truncated to the 2/3 box |kx|, |ky| <= floor((N-1)/3).
@@ -167,11 +171,17 @@ typedef struct lm_result {
 int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_device,
               void* stream, sw_handle** out);
 
-/* Release all memory of a handle (synchronises its stream).  NULL: no-op. */
+/* Release all memory of a handle (synchronises its stream).  NULL: no-op.
+ * (Sec. 2: each averaging interval is computed independently, so a handle
+ * holds no state beyond the current dynamics and its open interval; an open
+ * interval is discarded.) */
 void sw_destroy(sw_handle* h);
 
-/* Advance the shallow-water state only by nsteps >= 0 RK4 steps.
- * SW_EBUSY while an averaging interval is open.  Asynchronous. */
+/* Advance the shallow-water state only, Eq. (sw_eqs_dimless), by nsteps >= 0
+ * steps of the handle's stepper (sw_params.stepper: RK4, or the paper's Heun
+ * of Sec. 4.1 or forward Euler of Sec. 4.2.1, each with the integrating
+ * factor of the viscous term).  SW_EBUSY while an averaging interval is
+ * open.  Asynchronous. */
 int sw_step(sw_handle* h, int64_t nsteps);
 
 /* Open an averaging interval at tau = current time: zero the Lagrangian-mean
@@ -179,14 +189,20 @@ int sw_step(sw_handle* h, int64_t nsteps);
  * accumulators = 0).  SW_ESTATE if an interval is already open. */
 int lmean_begin(sw_handle* h, const lm_params* lp);
 
-/* Advance the dynamics and the open interval together by nsteps >= 0 RK4
- * steps (on-the-fly computation, Sec. 5).  SW_ERANGE if nsteps exceeds the
+/* Advance the dynamics and the open interval together by nsteps >= 0 steps
+ * of the handle's stepper (on-the-fly computation, Sec. 5): Strategy 1,
+ * Eq. (gtilde-evol) and the displacement form of Eq. (Xi-1evol); Strategy 2,
+ * Eqs. (xi_evol), (barf_xi); Eulerian accumulators, Eq. (ave).  SW_ERANGE if nsteps exceeds the
  * steps remaining, SW_ESTATE if no interval is open.  Asynchronous: the
  * steps are replays of a captured CUDA graph on the handle's stream. */
 int lmean_step(sw_handle* h, int64_t nsteps);
 
 /* Close a completed interval (remaining steps == 0, else SW_ESTATE) and write
- * the means (see lm_result) in FP64.  With host outputs it synchronises the
+ * the means (see lm_result) in FP64: Strategy 1, f~^L = g(tau+T)/T (Sec.
+ * 4.1, the division that follows Eq. (gtilde-evol)) and the mean positions
+ * Xi^{-1}(x, tau+T) = x - D/T (Sec. 3.1, Eq. (Xi-1evol)); Strategy 2,
+ * fbar^L = g/T and the lift map Xi = x + xi (Sec. 3.2, Eq. (Xievol); Sec.
+ * 4.2, Eqs. (xi_evol), (barf_xi)); Eulerian means E/T, Eq. (ave).  With host outputs it synchronises the
  * handle's stream; with device outputs (on_device = 1) it returns once the
  * work is enqueued on that stream. */
 int lmean_end(sw_handle* h, const lm_result* out);
@@ -265,8 +281,8 @@ typedef struct sw_batch sw_batch;
  * a failing create is given by sw_last_error(NULL). */
 int sw_batch_create(sw_handle* const* handles, int n, sw_batch** out);
 
-/* Advance every member by nsteps >= 0 RK4 steps (its dynamics, and its open
- * interval if it has one).  SW_ERANGE if nsteps exceeds the steps remaining
+/* Advance every member by nsteps >= 0 steps of the members' common stepper
+ * (its dynamics, and its open interval if it has one).  SW_ERANGE if nsteps exceeds the steps remaining
  * in a member's open interval (nothing is stepped then).  Asynchronous. */
 int sw_batch_step(sw_batch* b, int64_t nsteps);
 
@@ -277,6 +293,14 @@ int sw_batch_step(sw_batch* b, int64_t nsteps);
  * index in *choice (may be NULL).  The members' states are saved before the trials and
  * restored after them (temporary device copies).  Synchronises. */
 int sw_batch_tune(sw_batch* b, int trial_steps, int* choice);
+
+/* Set the row-pass launch shape that sw_batch_tune would pick as `choice`
+ * (4 * points index + pairs index, as above) without timing anything: for
+ * callers that replay a shape tuned earlier, and for tests that must cover
+ * every shape.  The members' arithmetic and results do not depend on it.
+ * SW_EINVAL if choice is outside 0..15 or its points per block are fewer
+ * than the largest member's N. */
+int sw_batch_set_shape(sw_batch* b, int choice);
 
 /* Kernels launched by the batch since its creation. */
 int sw_batch_launch_count(sw_batch* b, int64_t* count);

@@ -27,7 +27,7 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "lmean_progress", "sw_get_fields", "sw_set_fields", "sw_diag", "sw_get_state",
            "sw_set_state", "sw_time", "sw_sync", "sw_last_error", "sw_version", "sw_kernel_times",
            "sw_launch_count", "sw_project_static", "sw_batch_create", "sw_batch_step",
-           "sw_batch_tune", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
+           "sw_batch_tune", "sw_batch_set_shape", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
            "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
            "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap", "lmean_lift",
            "sw_spectrum", "sw_sl_create", "sw_sl_step", "sw_sl_end", "sw_sl_destroy")
@@ -136,6 +136,7 @@ def load(path: str = LIB_PATH):
         "sw_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(H)]),
         "sw_batch_step": (C.c_int, [H, C.c_int64]),
         "sw_batch_tune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
+        "sw_batch_set_shape": (C.c_int, [H, C.c_int]),
         "sw_batch_launch_count": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "sw_batch_last_error": (C.c_char_p, [H]),
         "sw_batch_destroy": (None, [H]),
@@ -346,6 +347,10 @@ def sw_batch_tune(b, trial_steps=8):
     return c.value
 
 
+def sw_batch_set_shape(b, choice):
+    _bcheck(load().sw_batch_set_shape(b, int(choice)), b)
+
+
 def sw_batch_launch_count(b):
     n = C.c_int64()
     _bcheck(load().sw_batch_launch_count(b, C.byref(n)), b)
@@ -445,11 +450,26 @@ def sw_server_destroy(s: Server):
 
 def sw_project_static(inp, out, N, stream=None):
     """Allocation-free projection of a device field onto the dealiased box
-    (see include/lagmean.h); inp, out: contiguous float64 CUDA tensors."""
-    pi, di = _ptr(inp)
-    po, do = _ptr(out)
-    if not (di and do):
-        raise ValueError("sw_project_static takes device tensors")
+    (see include/lagmean.h); inp, out: contiguous float64 CUDA tensors of
+    shape (N, N) on the current CUDA device (they may be the same tensor).
+    Shapes, dtypes and devices are checked before the library is called, so
+    a short buffer never reaches a kernel."""
+    N = int(N)
+    for name, t in (("inp", inp), ("out", out)):
+        if isinstance(t, np.ndarray) or not hasattr(t, "is_cuda"):
+            raise ValueError(f"sw_project_static: {name} must be a torch CUDA tensor")
+        if tuple(t.shape) != (N, N):
+            raise ValueError(f"sw_project_static: {name} has shape {tuple(t.shape)}, expected ({N}, {N})")
+        if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+            raise ValueError(f"sw_project_static: {name} must be contiguous float64")
+        if not t.is_cuda:
+            raise ValueError(f"sw_project_static: {name} must be on a CUDA device")
+    import torch
+    cur = torch.cuda.current_device()
+    if inp.device.index != cur or out.device.index != cur:
+        raise ValueError("sw_project_static: inp and out must be on the current CUDA device")
+    pi, _ = _ptr(inp)
+    po, _ = _ptr(out)
     lib = load()
     rc = lib.sw_project_static(pi, po, int(N), C.c_void_p(stream or 0))
     if rc != SW_OK:

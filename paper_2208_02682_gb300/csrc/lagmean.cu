@@ -1503,6 +1503,24 @@ extern "C" int sw_batch_tune(sw_batch* b, int trial_steps, int* choice) {
   return rc;
 }
 
+extern "C" int sw_batch_set_shape(sw_batch* b, int choice) {
+  if (!b) return SW_EINVAL;
+  b->err.clear();
+  static const int pts[4] = {256, 512, 1024, 2048};
+  static const int ppbs[4] = {1, 2, 3, MAXP};
+  if (choice < 0 || choice >= 16) return bfail(b, SW_EINVAL, "choice must be in 0..15");
+  BatchExec* ex = b->ex;
+  for (sw_handle* h : ex->members)
+    if (pts[choice / 4] < h->g.N) return bfail(b, SW_EINVAL, "points per block below a member's N");
+  for (sw_handle* h : ex->members) {
+    h->Bp = row_block_rows(h->g.N, pts[choice / 4]);
+    h->ppb = ppbs[choice % 4];
+    ++h->version;
+  }
+  b->tuned = choice;
+  return SW_OK;
+}
+
 extern "C" int sw_batch_launch_count(sw_batch* b, int64_t* count) {
   if (!b || !count) return SW_EINVAL;
   *count = b->ex->launches;

@@ -170,3 +170,27 @@ def test_sl_arguments_rejected_before_device_use(lm):
     assert lib.sw_sl_step(None, 1) == lm.api.SW_EINVAL
     assert lib.sw_sl_end(None, None) == lm.api.SW_EINVAL
     lib.sw_sl_destroy(None)  # no-op
+
+
+@pytest.mark.parametrize("case", ["short_in", "short_out", "host_array", "wrong_dtype", "cpu_tensor"])
+def test_project_static_rejects_bad_buffers_before_any_launch(lm, case):
+    # the binding checks shape, dtype and device before it calls the library,
+    # so a buffer shorter than N*N never reaches a kernel (no GPU needed here)
+    import torch
+    N = 64
+    good = torch.zeros((N, N), dtype=torch.float64)
+    inp, out = good, good
+    if case == "short_in":
+        inp = torch.zeros((N // 2, N), dtype=torch.float64)
+    elif case == "short_out":
+        out = torch.zeros((N, N - 1), dtype=torch.float64)
+    elif case == "host_array":
+        inp = np.zeros((N, N))
+    elif case == "wrong_dtype":
+        out = torch.zeros((N, N), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        lm.sw_project_static(inp, out, N)
+
+
+def test_batch_shape_setter_rejects_null(lm):
+    assert lm.api.load().sw_batch_set_shape(None, 0) == lm.api.SW_EINVAL

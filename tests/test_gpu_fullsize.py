@@ -1,11 +1,13 @@
 """Checks at the workloads' full sizes and step counts.
 
-* 64^2, one interval of 4 wave periods (1219 RK4 steps), Strategy 1, FP64:
-  element-wise against the oracle (which finishes this in seconds).
+* 64^2, one interval of 4 wave periods (1219 RK4 steps), Strategy 1, FP64
+  and FP32: element-wise against the oracle.
 * 256^2, one full interval (1097 steps) of Strategies 1 and 2 stepped as one
-  batch (the launch configuration bench.py times): the FP32 form against the
-  FP64 form on the GPU, per field, and properties that hold at any size:
-  bitwise mass conservation and the agreement of the two strategies through
+  batch (the launch configuration bench.py times), FP64 and FP32:
+  element-wise against the oracle (which takes minutes here and runs in a
+  worker process from the start of the session), the FP32 form against the
+  FP64 form on the GPU, and properties that hold at any size: bitwise mass
+  conservation and the agreement of the two strategies through
   Eq. (tildebar) at the order of the bilinear interpolation.
 * 1024^2 precision form, one interval: FP32 against FP64 per field.
 """
@@ -15,7 +17,7 @@ import pytest
 import sw_inputs as si
 from oracle import rel_l2
 
-from _helpers import FIELDS, compare, gpu, run_oracle_interval
+from _helpers import FIELDS, compare, gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -50,16 +52,17 @@ def _interval(lm, w, prec, strategies, batched=True):
     return outs, diag
 
 
-def test_plain64_full_interval_fp64_matches_oracle(lm):
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_plain64_full_interval_matches_oracle(lm, oracle_pool, prec, tol):
     w = si.WORKLOADS["plain-64"]
     assert w.n_steps == 1219
-    outs, _ = _interval(lm, w, "f64", (1,), batched=False)
-    ref, _ = run_oracle_interval(w.N, w.dt, w.initial_condition(), 1, w.n_steps, nu8=w.nu8)
+    outs, _ = _interval(lm, w, prec, (1,), batched=False)
+    ref, _ = oracle_pool.result("plain64-s1-full")
     e = compare(outs[0], ref, w.N, 1)
-    assert max(e.values()) < 1e-12, e
+    assert max(e.values()) < tol, e
 
 
-def test_plain256_full_interval_batched(lm):
+def test_plain256_full_interval_batched(lm, oracle_pool):
     w = si.WORKLOADS["plain-256"]
     assert w.n_steps == 1097
     o32, d32 = _interval(lm, w, "f32", (1, 2))
@@ -67,6 +70,13 @@ def test_plain256_full_interval_batched(lm):
     for s in range(2):
         e = compare(o32[s], o64[s], w.N, s + 1)
         assert max(e.values()) < 2e-5, (s + 1, e)
+    # element by element against the oracle over the whole interval
+    for s in range(2):
+        ref, _ = oracle_pool.result(f"plain256-s{s + 1}-full")
+        e64 = compare(o64[s], ref, w.N, s + 1)
+        assert max(e64.values()) < 1e-12, ("f64", s + 1, e64)
+        e32 = compare(o32[s], ref, w.N, s + 1)
+        assert max(e32.values()) < 2e-5, ("f32", s + 1, e32)
     # mass: <h> is the k = 0 depth coefficient, unchanged bit for bit in FP64
     h0 = float(np.mean(w.initial_condition()[2]))
     for d in d64:

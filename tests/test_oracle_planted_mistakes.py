@@ -26,6 +26,8 @@ PLANTS = [
     ("sw_lagmean.py", "return 1j * self.ky * zh * inv, -1j * self.kx * zh * inv",
      "return 1j * self.kx * zh * inv, -1j * self.ky * zh * inv",
      "tests/test_oracle_euler2d.py::test_velocity_from_vorticity_and_steady_cellular_flow"),
+    ("sw_lagmean.py", "wx = 0.5 * au", "wx = 1.0 * au",
+     "tests/test_oracle_steppers.py::test_strategy2_uniform_flow_exact"),
     ("sw_lagmean.py", 'even = lm["done"] % 2 == 0', 'even = lm["done"] % 2 == 1',
      "tests/test_oracle_steppers.py::test_xi_first_uniform_flow_exact"),
     ("gbla.py", "ddx, ddy = -dt * ux, -dt * uy", "ddx, ddy = dt * ux, dt * uy",

@@ -35,6 +35,36 @@ def test_uniform_inertial_oscillation(stepper):
 
 
 @pytest.mark.parametrize("stepper", ["euler", "heun", "rk4"])
+@pytest.mark.parametrize("n", [1, 2, 9])
+def test_strategy2_uniform_flow_exact(stepper, n):
+    # Strategy 2 (Eqs. xi_evol, barf_xi) in a uniform flow U with f0 = 0: the
+    # flow stays uniform and every gradient vanishes, so the equations reduce
+    # to d xi/ds = U - xi/s and d g/ds = f(x + xi) = U, whose solutions from
+    # xi = g = 0 are xi = U s/2 (the partial mean position of Eq. (barphi)
+    # moves at half the particle speed) and g = U s.  Forward Euler's first
+    # step is xi_1 = dt (U - w(0)), so it reproduces them only with the limit
+    # w = u/2 at s = 0; Heun and RK4 are exact for any value of that limit
+    # (their later stages cancel it), which this also checks: the stage
+    # combinations of every stepper carry the -w term and the stage times.
+    N, dt, U0, V0 = 16, 5e-3, 0.7, -0.3
+    u, v, h = si.uniform_flow(N, U0, V0)
+    o = SWOracle(N, dt, u, v, h, f0=0.0, stepper=stepper)
+    o.lmean_begin(2, fields=("zeta", "h", "u", "v"), pos=True, eulerian=True, n_steps=n)
+    o.lmean_step(n)
+    r = o.lmean_end()
+    T = n * dt
+    x = 2 * np.pi * np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    np.testing.assert_allclose(r["pos_x"] - X, U0 * T / 2, atol=1e-15)
+    np.testing.assert_allclose(r["pos_y"] - Y, V0 * T / 2, atol=1e-15)
+    np.testing.assert_allclose(r["u"], U0, atol=1e-14)
+    np.testing.assert_allclose(r["v"], V0, atol=1e-14)
+    np.testing.assert_allclose(r["h"], 1.0, atol=1e-14)
+    np.testing.assert_allclose(r["zeta"], 0.0, atol=1e-14)
+    np.testing.assert_allclose(r["E_u"], U0, atol=1e-14)
+
+
+@pytest.mark.parametrize("stepper", ["euler", "heun", "rk4"])
 def test_laplacian_integrating_factor_exact(stepper):
     N, dt, f0, n = 16, 1e-2, 1.3, 120
     kx, ky = 2, 1
