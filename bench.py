@@ -120,8 +120,56 @@ def peaks():
 
 
 # ------------------------------------------------------------------------------
+def _oracle_run(task):
+    """Worker: one bounded oracle sample (strategy, steps) of a named workload;
+    returns the wall-clock start and end of its stepping (time.time)."""
+    name, strategy, steps = task
+    from oracle import SWOracle
+    w = si.WORKLOADS[name]
+    u, v, h = w.initial_condition()
+    o = SWOracle(w.N, w.dt, u, v, h, f0=w.f0, c2=w.c2, nu8=w.nu8)
+    o.lmean_begin(strategy, fields=FIELDS, pos=True, eulerian=True, n_steps=steps)
+    t0 = time.time()
+    o.lmean_step(steps)
+    return t0, time.time()
+
+
+def _ready(_):
+    import oracle  # noqa: F401  (imports numpy and the oracle before the timed tasks)
+    time.sleep(0.3)  # hold this worker so that every worker takes one of these tasks
+    return os.getpid()
+
+
+class OraclePool:
+    """The FP64 oracle on all host cores: one worker process per core (spawn
+    start method), each running a bounded sample of the workload, the
+    strategies alternating over the workers.  The oracle itself is unchanged
+    (numpy, one thread per process); throughput = all workers' grid-point-steps
+    over the wall-clock span from the first start to the last end."""
+
+    def __init__(self, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = int(workers or os.cpu_count() or 1)
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"))
+        # start every worker process before anything is timed
+        for _ in range(5):
+            if len(set(self.ex.map(_ready, range(self.workers)))) == self.workers:
+                break
+
+    def sample(self, w, steps):
+        tasks = [(w.name, w.strategies[i % len(w.strategies)], steps) for i in range(self.workers)]
+        spans = list(self.ex.map(_oracle_run, tasks))
+        wall = max(b for _, b in spans) - min(a for a, _ in spans)
+        gp = self.workers * w.N * w.N * steps
+        return gp / wall, wall
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
 def oracle_sample(w, steps_per_strategy):
-    """Time the FP64 oracle on a bounded sample of the workload (both strategies)."""
+    """Time the FP64 oracle on one core on a bounded sample of the workload (both strategies)."""
     from oracle import SWOracle
     u, v, h = w.initial_condition()
     t0 = time.perf_counter()
@@ -140,22 +188,27 @@ def run_reference(args):
         return
     w = workload()
     sample = 12
+    pool = OraclePool()
     for _ in range(args.warmup):
-        oracle_sample(w, 2)
-    vals, tot = [], 0.0
+        pool.sample(w, 2)
+    tot, gp = 0.0, 0
     for _ in range(args.steps):
-        v, dt = oracle_sample(w, sample)
-        vals.append(v)
+        v, dt = pool.sample(w, sample)
         tot += dt
-    value = len(vals) * len(w.strategies) * w.N * w.N * sample / tot
+        gp += pool.workers * w.N * w.N * sample
+    pool.close()
+    value = gp / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": config_dict(w, "oracle f64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} RK4 steps per strategy of the {w.N}^2 workload per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                         "host_cores": os.cpu_count(),
+                         "sample": f"per step, {pool.workers} concurrent oracle processes (one per host core, "
+                                   f"numpy FP64, one thread each), each {sample} RK4 steps of the {w.N}^2 "
+                                   f"workload, Strategies 1 and 2 alternating over the processes"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -257,9 +310,86 @@ def measure_precision(lm, torch):
         elif k == "pos_y":
             a, b = a - Y, b - Y
         err[k] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    fp64_peak = lm.sw_fma_peak("f64")
+    fp32_peak = lm.sw_fma_peak("f32")
+    flops = 4 * fft_flops_per_stage(N) * n
+    fp64 = {"achieved_tflops": flops / (times["f64"] * 1e-3) / 1e12, "peak_tflops": fp64_peak,
+            "unit": "TFLOP/s", "bound": "alu",
+            "note": "conventional FFT flop count (5 n log2 n per transform) of the interval over its FP64 device "
+                    "time, against the measured FP64 FMA rate of the CUDA cores (sw_fma_peak)"}
+    fp64["frac"] = fp64["achieved_tflops"] / fp64_peak
     return {"N": N, "n_steps": n, "rel_l2_fp32_vs_fp64": err, "max_rel_l2": max(err.values()),
             "gp_steps_per_s": {p: N * N * n / (t * 1e-3) for p, t in times.items()},
+            "fp64_path": fp64, "fp32_fma_peak_tflops": fp32_peak,
             "workload": "1024^2, Ro 0.05, waves |k| 8-12, ratio 2, Strategy 1, one interval"}
+
+
+# Algorithmic bytes per grid-point-step of the coupled FP32 Strategy-1 step
+# (13 evolved fields) under the three-sweep model: column inverse pass,
+# row pass with the products on chip, column forward pass with the RK
+# update, about 63 words per grid point and stage.
+MODEL_BYTES_FP32 = 1010.0
+
+
+def fft_flops_per_stage(N, strategy=1):
+    """Conventional FFT flop count (5 n log2 n per complex n-point transform)
+    of one stage of the Strategy-1 configuration with zeta, h, u, v,
+    positions and Eulerian means: 16 column inverse and 11 column forward
+    transforms over the K+1 retained columns, and 14 row transforms per row
+    (u, v, h, zeta and six gradient pairs inverse, six product pairs forward)."""
+    K = (N - 1) // 3
+    lg = int(round(np.log2(N)))
+    return 5.0 * N * lg * (27 * (K + 1) + 14 * N)
+
+
+def measure_large_grids(lm, torch, sizes=(1024, 2048), steps=4, graph_steps=8):
+    """The bandwidth-relevant sizes (working set far above the 129 MB L2):
+    FP32 Strategy 1 with zeta, h, u, v, positions and Eulerian means on the
+    precision form's generator (Ro 0.05, waves |k| 8-12, ratio 2).  Per size:
+    the step from the captured graph (CUDA events), the per-kernel device
+    times with each kernel launched alone (sw_kernel_times), the dominant
+    kernel's roofline, and the whole step against the three-sweep byte model
+    and against the kernels' own algorithmic bytes."""
+    peak, src = peaks()
+    res = {}
+    for N in sizes:
+        K = (N - 1) // 3
+        dt = 5e-3 if N <= 1024 else 2e-3
+        ic = np.ascontiguousarray(np.stack(si.turbulence_plus_waves(N, 0.05, 2.0, 8.0, 12.0, 1003)))
+        h = lm.sw_create(lm.make_params(N, dt, precision="f32", nu8=10.0 / K ** 8), ic)
+        lm.lmean_begin(h, lm.make_lm_params(1, FIELDS, pos=True, eulerian=True, n_steps=2 * graph_steps + steps))
+        lm.lmean_step(h, graph_steps)  # graph capture and upload, warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lm.lmean_step(h, graph_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / graph_steps
+        kt = lm.sw_kernel_times(h, steps)
+        lm.sw_destroy(h)
+        per = {k: {"ms_per_launch": t / c, "launches": c, "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9,
+                   "frac": (b / c) / (t / c * 1e-3) / 1e9 / peak}
+               for k, (t, c, b) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+        dom = max(kt, key=lambda k: kt[k][0])
+        t_ms, cnt, byt = kt[dom]
+        achieved = (byt / cnt) / (t_ms / cnt * 1e-3) / 1e9
+        step_bytes = sum(b for (_, _, b) in kt.values()) / steps
+        gps = N * N / (step_ms * 1e-3)
+        res[str(N)] = {
+            "step_ms": step_ms, "gp_steps_per_s": gps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": measured_traffic(dom, N), "kernel": dom,
+                         "peak_source": src},
+            "step_model_bytes_per_gp_step": MODEL_BYTES_FP32,
+            "step_model_frac": gps * MODEL_BYTES_FP32 / 1e9 / peak,
+            "step_kernel_bytes_per_gp_step": step_bytes / (N * N),
+            "step_kernel_bytes_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
+            "kernels": per,
+        }
+    res["workload"] = ("FP32 Strategy 1 (zeta, h, u, v, positions, Eulerian), turbulence Ro 0.05 + waves |k| 8-12 "
+                       "(ratio 2), dt 5e-3 (1024^2) / 2e-3 (2048^2); kernels timed one by one, warm")
+    return res
 
 
 def measure_remap(lm, torch, outs, strategies, iters=20):
@@ -444,17 +574,32 @@ def measure_vortex_merger(lm, torch, N=128, dt=5e-3, T=25.0):
     return res
 
 
-def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1005):
-    """Poisson stream of Lagrangian-mean requests through sw_server."""
+def served_dt(N, f0=1.0, c2=1.0):
+    """Time step of a served job (reading G10): RK4 stays stable on the
+    imaginary axis for |omega| dt <= 2 sqrt 2; with the fastest gravity wave
+    omega_max = sqrt(f0^2 + 2 c2 K^2), dt = 5e-3 while omega_max dt stays
+    within 0.9 of that bound (up to 1024^2), else 2/omega_max (2.07e-3 at
+    2048^2)."""
+    K = (N - 1) // 3
+    wmax = float(np.sqrt(f0 * f0 + 2.0 * c2 * K * K))
+    return 5e-3 if wmax * 5e-3 <= 0.9 * 2.0 * np.sqrt(2.0) else 2.0 / wmax
+
+
+def measure_served(lm, n_jobs=40, rate=50.0, sizes=(128, 256, 512, 1024, 2048), seed=1005):
+    """Poisson stream of Lagrangian-mean requests through sw_server: grids
+    uniform over `sizes`, averaging windows uniform in 1-8 wave periods
+    (period 2 pi/omega(|k| = 4)), strategy 1 or 2, FP32 with FP64 recovery,
+    150 GB budget, one private stream per batch group."""
     import time as _t
     rng = np.random.Generator(np.random.PCG64(seed))
+    period = 2 * np.pi / si.wave_frequency(4.0, 1.0, 1.0)
     jobs = []
     for i in range(n_jobs):
         N = int(rng.choice(sizes))
         periods = float(rng.uniform(1.0, 8.0))
         strat = int(rng.choice([1, 2]))
-        dt = 5e-3 if N <= 1024 else 2.5e-3
-        n = si.interval_steps(periods, 4.0, dt)
+        dt = served_dt(N)
+        n = max(1, int(round(periods * period / dt)))
         K = (N - 1) // 3
         ic = np.stack(si.turbulence_plus_waves(N, 0.1, 1.0, 4.0, 6.0, 3000 + i))
         out = {k: np.zeros((N, N)) for k in ("zeta", "h", "u", "v", "pos_x", "pos_y")}
@@ -471,29 +616,37 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024), seed=1
         lm.sw_server_submit(srv, lm.make_params(N, dt, precision="f32", nu8=10.0 / K ** 8),
                             lm.make_lm_params(strat, ("zeta", "h", "u", "v"), n_steps=n), ic, out, tag=i)
     done = []
-    while len(done) < n_jobs and _t.time() - t_start < 600:
+    while len(done) < n_jobs and _t.time() - t_start < 3600:
         done += lm.sw_server_poll(srv, wait_ms=100)
     st = lm.sw_server_stats_get(srv)
     lm.sw_server_destroy(srv)
     lat = np.array([d["t_done"] - d["t_submit"] for d in done])
     t0 = min(d["t_submit"] for d in done)
     t1 = max(d["t_done"] for d in done)
-    offered = sum(j[0] * j[0] * j[3] for j in jobs) / (n_jobs / rate)
+    span = n_jobs / rate
+    offered = sum(j[0] * j[0] * j[3] for j in jobs) / span
+    by_size = {}
+    for N in sizes:
+        l = np.array([d["t_done"] - d["t_submit"] for d in done if jobs[d["tag"]][0] == N])
+        if len(l):
+            by_size[str(N)] = {"jobs": int(len(l)), "p50_s": float(np.percentile(l, 50)),
+                               "p99_s": float(np.percentile(l, 99))}
     return {"jobs": n_jobs, "completed": st["completed"], "failed": st["failed"],
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "throughput": st["grid_point_steps"] / (t1 - t0), "unit": UNIT,
-            "offered_load": offered, "peak_bytes": st["peak_bytes"], "rounds": st["rounds"],
+            "offered_load": offered, "achieved_over_offered": st["grid_point_steps"] / (t1 - t0) / offered,
+            "latency_by_size": by_size, "peak_bytes": st["peak_bytes"], "rounds": st["rounds"],
+            "dt": {str(N): served_dt(N) for N in sizes},
             "workload": f"Poisson {rate:g} req/s, N uniform in {list(sizes)}, windows U[1,8] wave periods, "
                         "strategy 1 or 2, FP32, 150 GB budget, %d requests" % n_jobs}
 
 
-# DRAM bytes per launch of the dominant kernel, from one ncu capture of this
-# bench's timed region (profiles/traffic_rowprod_bench256.md: mean of the warm
-# launches, each covering both runs of the batch); valid only while the
-# stage-kernel sources are those of that capture (the hash is refreshed with
-# each capture).
-TRAFFIC_CAPTURE = {"kernel": "row_prod", "bytes": 257060.6, "runs_per_launch": 2,
-                   "sources_sha256": "e195043a98b708dc3418ab9e832de9659c538e66aa50e28cdec5ad794177c411"}
+# DRAM bytes per launch of a kernel for one run, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum) summarised in profiles/;
+# keyed by (kernel, N).  Valid only while the stage-kernel sources are those
+# of the captures (their hash below); otherwise `traffic` is reported null.
+TRAFFIC_CAPTURES = {}
+TRAFFIC_SOURCES_SHA256 = None
 
 
 # the sources that define the stage kernels and their launch shapes
@@ -511,13 +664,13 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(kernel):
-    """Per launch of one run, like `achieved` (the captured batched launch
-    covers runs_per_launch runs)."""
-    c = TRAFFIC_CAPTURE
-    if kernel != c["kernel"] or kernel_sources_sha256() != c["sources_sha256"]:
+def measured_traffic(kernel, N):
+    """DRAM bytes per launch of one run, like `achieved`; None without a
+    capture of the current sources."""
+    c = TRAFFIC_CAPTURES.get((kernel, int(N)))
+    if c is None or kernel_sources_sha256() != TRAFFIC_SOURCES_SHA256:
         return None
-    return c["bytes"] / c["runs_per_launch"]
+    return c
 
 
 def run_ours(args):
@@ -618,7 +771,7 @@ def run_ours(args):
     peak, peak_src = peaks()
     achieved = (byt / cnt) / (t_ms / cnt * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": measured_traffic(dom), "kernel": dom,
+                "frac": achieved / peak, "traffic": measured_traffic(dom, N), "kernel": dom,
                 "peak_source": peak_src,
                 "note": "the 256^2 working set (about 20 MB) stays in L2: at this size the row pass is latency-bound, not DRAM-bound"}
     kernel_share = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / tot,
@@ -668,6 +821,7 @@ def run_ours(args):
         extras["vortex_merger"] = measure_vortex_merger(lm, torch)
         extras["batched"] = measure_batched(lm, torch)
         extras["precision_form"] = measure_precision(lm, torch)
+        extras["large_grids"] = measure_large_grids(lm, torch)
         extras["served"] = measure_served(lm, n_jobs=args.serve_jobs)
 
     if rank != 0:
@@ -677,9 +831,16 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         sample = 12
-        v, dt = oracle_sample(w, sample)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample} RK4 steps of each strategy at {N}^2 ({dt:.1f} s, numpy FP64, one thread)"}
+        pool = OraclePool()
+        v, dt = pool.sample(w, sample)
+        pool.close()
+        v1, dt1 = oracle_sample(w, sample)
+        cpu = {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "host_cores": os.cpu_count(),
+               "sample": f"{pool.workers} concurrent oracle processes (one per host core, numpy FP64, one thread "
+                         f"each), each {sample} RK4 steps of the {N}^2 workload, Strategies 1 and 2 alternating "
+                         f"over the processes ({dt:.1f} s wall)",
+               "single_core_value": v1,
+               "single_core_sample": f"{sample} RK4 steps of each strategy, one process ({dt1:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -706,7 +867,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, precision and served figures")
-    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-jobs", type=int, default=40,
+                    help="requests in the served stream (the full serving form is 200)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -330,7 +330,8 @@ typedef struct sw_server_params {
   int32_t chunk_steps; /* RK4 steps per round, >= 1                          */
   int32_t reserved;    /* must be 0                                         */
   int64_t hbm_budget;  /* bytes of device memory for job state, > 0         */
-  void* stream;        /* cudaStream_t for all job work (NULL: a private one) */
+  void* stream;        /* cudaStream_t for all job work; NULL: one private
+                          stream per group, so that groups overlap          */
 } sw_server_params;
 
 typedef struct sw_job {
@@ -533,6 +534,18 @@ int sw_sl_end(sl_interval* s, const lm_result* out);
 
 /* Free an interval without results.  NULL: no-op. */
 void sw_sl_destroy(sl_interval* s);
+
+/* ---- measurement ------------------------------------------------------------
+ * Fused-multiply-add rate of this GPU's CUDA cores in TFLOP/s (2 flops per
+ * FMA), for the arithmetic roofline of the transform kernels: the FP64 path
+ * is bound by its FP64 arithmetic, which runs on these cores.  Runs
+ * 8 x (multiprocessors) blocks of 256 threads, each with 8 independent FMA
+ * chains of 16 x trips FMAs, and reports the best of five timed launches
+ * (CUDA events on `stream`, after one warm-up launch).  Allocates a small
+ * scratch buffer; synchronises.  The paper has no counterpart.
+ *   precision: SW_PREC_FP64 or SW_PREC_FP32; trips: 1..2^20 (4096 is ample).
+ * Errors: SW_EINVAL, SW_ECUDA (message via sw_last_error(NULL)). */
+int sw_fma_peak(int precision, int trips, double* tflops, void* stream);
 
 /* Wait for all device work of the handle. */
 int sw_sync(sw_handle* h);

@@ -14,5 +14,5 @@ from .api import (  # noqa: F401
     sw_batch_launch_count, sw_batch_last_error, sw_batch_destroy, sw_server_create, sw_server_submit,
     sw_server_poll, sw_server_stats_get, sw_server_clock, sw_server_destroy, sw_state_bytes,
     lmean_remap, lmean_lift, sw_spectrum, spectrum_shells, make_sl_params, sw_sl_create, sw_sl_step,
-    sw_sl_end, sw_sl_destroy,
+    sw_sl_end, sw_sl_destroy, sw_fma_peak,
 )

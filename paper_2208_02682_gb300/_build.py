@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblagmean.so")
-SOURCES = ["lagmean.cu", "kernels_f32.cu", "kernels_f64.cu", "project_static.cu", "server.cu", "remap.cu", "gbla.cu"]
+SOURCES = ["lagmean.cu", "kernels_f32.cu", "kernels_f64.cu", "project_static.cu", "server.cu", "remap.cu", "gbla.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

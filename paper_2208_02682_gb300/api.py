@@ -30,7 +30,7 @@ EXPORTS = ("sw_create", "sw_destroy", "sw_step", "lmean_begin", "lmean_step", "l
            "sw_batch_tune", "sw_batch_set_shape", "sw_batch_launch_count", "sw_batch_last_error", "sw_batch_destroy",
            "sw_server_create", "sw_server_submit", "sw_server_poll", "sw_server_stats_get",
            "sw_server_clock", "sw_server_destroy", "sw_state_bytes", "lmean_remap", "lmean_lift",
-           "sw_spectrum", "sw_sl_create", "sw_sl_step", "sw_sl_end", "sw_sl_destroy")
+           "sw_spectrum", "sw_sl_create", "sw_sl_step", "sw_sl_end", "sw_sl_destroy", "sw_fma_peak")
 SW_K_NAMES = ("col_inv", "row_inv", "row_prod", "col_fwd", "update", "phys_q")
 SW_K_COUNT = 8
 
@@ -148,6 +148,7 @@ def load(path: str = LIB_PATH):
         "sw_server_destroy": (None, [H]),
         "sw_state_bytes": (C.c_int64, [C.POINTER(sw_params)]),
         "sw_version": (C.c_char_p, []),
+        "sw_fma_peak": (C.c_int, [C.c_int, C.c_int, _DP, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -605,6 +606,17 @@ def sw_sl_end(s, out: dict):
 
 def sw_sl_destroy(s):
     load().sw_sl_destroy(s[0])
+
+
+def sw_fma_peak(precision="f64", trips=4096, stream=None):
+    """FMA rate of the CUDA cores in TFLOP/s (see include/lagmean.h)."""
+    lib = load()
+    t = C.c_double(0.0)
+    rc = lib.sw_fma_peak({"f64": SW_PREC_FP64, "f32": SW_PREC_FP32}[precision], int(trips), C.byref(t),
+                         C.c_void_p(stream or 0))
+    if rc != SW_OK:
+        raise SWError(rc, lib.sw_last_error(None).decode())
+    return t.value
 
 
 def sw_last_error(h=None):

@@ -127,6 +127,11 @@ struct Layout {
   int p_zv, p_zu, p_ke, p_hu, p_hv, p_q;
   int p_g[NLMF];
   int p_p[2];
+  // some pair (2q, 2q+1) of the row pass has a second product that needs a
+  // transform or gather of its own (only when the products are not all
+  // paired heavy-with-light, e.g. the kinematic model)
+  int heavy2;
+  int pad_;
 };
 
 // discretisation of the mean equations (the C ABI's LM_SCHEME_* values)

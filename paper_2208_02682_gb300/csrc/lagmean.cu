@@ -223,6 +223,9 @@ static Layout build_layout(const sw_params& p, int strategy, int fields, int eul
     for (int j = 0; j < NLMF; ++j) remap(L.p_g[j]);
     remap(L.p_p[0]);
     remap(L.p_p[1]);
+    L.heavy2 = 0;
+    for (int q = 1; q < np; q += 2)
+      if (heavy(L.pk[q])) L.heavy2 = 1;
   }
   L.ni = ni;
   L.np = np;
@@ -268,9 +271,12 @@ static KBytes kernel_bytes(const sw_handle* h, const Layout& L) {
   int nk = 0;
   for (int f = 0; f < L.nf; ++f) nk += L.fkahan[f];
   const double nf = L.nf, np = L.np;
+  // integrating-factor tables: E per class at every stage; the stage that
+  // commits y_{n+1} also reads E^2 as hi + lo
   b.update[0] = (nf + np + 2 * nf) * MB * cs + 2 * MB * ts;
   b.update[1] = b.update[2] = (3 * nf + np + 2 * nf) * MB * cs + 2 * MB * ts;
-  b.update[3] = (3 * nf + np + nf + (h->fp32 ? 2 * nk : 0)) * MB * cs + 2 * MB * ts;
+  b.update[3] = (3 * nf + np + nf + (h->fp32 ? 2 * nk : 0)) * MB * cs + 6 * MB * ts;
+  if (h->p.stepper != SW_STEP_RK4) b.update[1] += 4 * MB * ts;
   return b;
 }
 
@@ -397,7 +403,7 @@ static int batch_build_t(BatchExec* b) {
     const sw_handle* h = b->members[r];
     const int npairs = (h->L.np + 1) / 2;
     const int npb = (h->ppb == 0 || h->ppb > npairs) ? npairs : h->ppb;
-    const int w = row_prod_groups<T>(h->g.N, h->Bp, npb, h->L.strategy);
+    const int w = row_prod_groups<T>(h->g.N, h->Bp, npb, h->L);
     W = w < W ? w : W;
   }
   if (n == 0) W = 1;
@@ -414,7 +420,7 @@ static int batch_build_t(BatchExec* b) {
                                ((1 << h->lC) * N) / 8, 256};
     const size_t sm[KT_COUNT] = {(size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs,
                                  (size_t)2 * h->Bi * row_stride<T>(N) * cs, 0,
-                                 row_prod_smem<T>(N, h->Bp, W, h->L.strategy),
+                                 row_prod_smem<T>(N, h->Bp, W, h->L),
                                  (size_t)(1 << h->lC) * col_buf_stride<T>(N, 1 << h->lC) * cs, 0};
     const KBytes kb = kernel_bytes(h, h->L);
     const double by[KT_COUNT] = {kb.col_inv, kb.row_inv, kb.phys_q, kb.row_prod, kb.col_fwd, 0.0};
@@ -728,9 +734,14 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static const int DIAG_BLOCKS = 1024;
 
 // Grid geometry: cutoff K, column tiles of C = 2048/N columns (at most 32:
-// C*N is the same for all grids up to 2048, so they can share batched
-// launches) and the padded column count KXP (a multiple of C and of 4).
-static void plan_geometry(int N, Geom& g, int& lC) {
+// C*N is the same for all grids up to 512, so they can share batched
+// launches; in FP32 at least 4, so that the lanes of a warp move 32-byte runs
+// of a row: one-column tiles at 2048^2 used a quarter of every 32-byte
+// sector of their strided accesses) and the padded column count KXP (a
+// multiple of C and of 4).  FP64 keeps C*N = 2048 (256 threads per column
+// block): its column passes are bound by FP64 arithmetic, and four FP64
+// columns of 2048 points would not fit in shared memory.
+static void plan_geometry(int N, size_t tsz, Geom& g, int& lC) {
   g.N = N;
   g.log2N = 0;
   while ((1 << g.log2N) < g.N) ++g.log2N;
@@ -740,6 +751,7 @@ static void plan_geometry(int N, Geom& g, int& lC) {
   // elements (256 threads); KXP stays a multiple of 4 for the generic passes
   lC = 0;
   while ((1 << lC) * g.N < 2048 && lC < 5) ++lC;
+  if (tsz == 4 && lC < 2) lC = 2;
   const int C = 1 << lC;
   const int pad = C > 4 ? C : 4;
   g.KXP = (g.KX + pad - 1) / pad * pad;
@@ -762,7 +774,7 @@ static ArenaPlan plan_arena(const Geom& g, size_t tsz) {
       MAXF * g.ms * cs, MAXF * g.ms * cs, MAXF * g.ms * cs, MAXF * g.ms * cs,  // y, ys, ys2, acc
       MAXF * g.ms * cs, MAXP * g.ms * cs,                                      // comp, ps
       MAXI * g.mi * cs, MAXP * g.mi * cs,                                      // mix, pmix
-      NPH * g.np * tsz, 2 * g.ms * tsz, g.N * cs,                              // phys, ef, tw
+      NPH * g.np * tsz, 6 * g.ms * tsz, g.N * cs,                              // phys, ef, tw
       g.N * sizeof(double2), 4 * g.ms * sizeof(double2),                       // tw64, spec64
       4 * g.mi * sizeof(double2), 12 * g.np * sizeof(double),                  // mix64, out64
       2 * DIAG_BLOCKS * sizeof(double), 4 * sizeof(double),                    // part, dres
@@ -781,8 +793,9 @@ extern "C" int64_t sw_state_bytes(const sw_params* p) {
   if (validate(p, why) != SW_OK) return 0;
   Geom g;
   int lC;
-  plan_geometry(p->N, g, lC);
-  return (int64_t)plan_arena(g, p->precision == SW_PREC_FP32 ? 4 : 8).total;
+  const size_t tsz = p->precision == SW_PREC_FP32 ? 4 : 8;
+  plan_geometry(p->N, tsz, g, lC);
+  return (int64_t)plan_arena(g, tsz).total;
 }
 
 template <typename T>
@@ -795,8 +808,21 @@ static void host_tables(const sw_params& p, const Geom& g, void* ef_host, void* 
       const double k2 = (double)kx * kx + ky * ky;
       const double k8 = p.visc == SW_VISC_LAPLACE ? k2 : k2 * k2 * k2 * k2;  // |k|^2p
       const long long m = (long long)kyi * g.KXP + kx;
-      ef[m] = (T)std::exp(-p.nu8 * k8 * p.dt * 0.5);
-      ef[g.ms + m] = (T)std::exp(-p.lm_nu8 * k8 * p.dt * 0.5);
+      // per class (dynamics, mean fields): E = exp(-nu |k|^2p dt/2) for the
+      // stage values, and E^2 as an unevaluated sum hi + lo for the commit
+      // of y_{n+1} = E^2 y_n + ...: rounded to T alone, E^2 would move every
+      // damped mode by up to half an ulp of T per step, an error that grows
+      // linearly with the steps of an interval (in FP32 about 4e-5 after
+      // 1219 steps at 64^2); hi + lo carries it to about twice T's digits.
+      const double nus[2] = {p.nu8, p.lm_nu8};
+      for (int c = 0; c < 2; ++c) {
+        const double E = std::exp(-nus[c] * k8 * p.dt * 0.5);
+        const double E2 = E * E;
+        const T hi = (T)E2;
+        ef[(3 * c) * g.ms + m] = (T)E;
+        ef[(3 * c + 1) * g.ms + m] = hi;
+        ef[(3 * c + 2) * g.ms + m] = (T)(E2 - (double)hi);
+      }
     }
   std::vector<double> re(g.N, 1.0), im(g.N, 0.0);
   fft_twiddle_table(g.log2N, re.data(), im.data());
@@ -829,7 +855,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   h->fp32 = p->precision == SW_PREC_FP32;
   h->tsz = h->fp32 ? 4 : 8;
   Geom& g = h->g;
-  plan_geometry(p->N, g, h->lC);
+  plan_geometry(p->N, h->tsz, g, h->lC);
   const size_t cs = 2 * h->tsz;  // complex T
   h->diag_blocks = DIAG_BLOCKS;
   h->Bp = row_block_rows(g.N);
@@ -857,7 +883,7 @@ extern "C" int sw_create(const sw_params* p, const double* ic_uvh, int ic_on_dev
   h->part = (double*)(base + o_part); h->dres = (double*)(base + o_dres);
   h->ctr = (long long*)(base + o_ctr); h->ticket = (unsigned*)(base + o_ticket);
   // tables
-  const size_t ef_bytes = 2 * g.ms * h->tsz, tw_bytes = g.N * cs;
+  const size_t ef_bytes = 6 * g.ms * h->tsz, tw_bytes = g.N * cs;
   char* hbuf = (char*)std::malloc(ef_bytes + tw_bytes + g.N * sizeof(double2));
   if (!hbuf) {
     cudaFree(h->arena);

@@ -22,8 +22,8 @@ inline int row_block_rows(int N, int points = 512) {
 
 // Row pass: B rows per block, W groups of N/8 threads per row (see
 // k_stage_row_prod); the block may hold up to row_prod_max_threads threads.
-template <typename T> size_t row_prod_smem(int N, int B, int W, int strategy) {
-  const size_t nur = strategy == 2 ? 6 : 4, nug = (size_t)row_prod_group_rows(strategy, N);
+template <typename T> size_t row_prod_smem(int N, int B, int W, const Layout& L) {
+  const size_t nur = L.strategy == 2 ? 6 : 4, nug = (size_t)row_prod_group_rows(L);
   return (size_t)B * nur * N * sizeof(T) +
          (size_t)B * W * (2 * row_stride<T>(N) * sizeof(cplx<T>) + nug * N * sizeof(T));
 }
@@ -32,12 +32,13 @@ template <typename T> size_t row_prod_smem(int N, int B, int W, int strategy) {
 // warps per group (N >= 256), a thread count within the block limit, at most
 // 15 named barriers (groups of N >= 512) and at most 110 KB of shared memory
 // (two blocks per SM; one resident block per SM made the wider shape slower).
-template <typename T> int row_prod_groups(int N, int B, int npb, int strategy) {
+template <typename T> int row_prod_groups(int N, int B, int npb, const Layout& L) {
+  const int strategy = L.strategy;
   const int G = N / 8;
   if (G < 32) return 1;
   int W = npb < 1 ? 1 : npb;
   while (W > 1 && (B * W * G > row_prod_max_threads<T>() || (G >= 64 && B * W > 15) ||
-                   row_prod_smem<T>(N, B, W, strategy) > (size_t)110 * 1024))
+                   row_prod_smem<T>(N, B, W, L) > (size_t)110 * 1024))
     --W;
   // Strategy 2 transforms one base pair (xi) before the products, so the
   // row's other groups wait at the barrier; that pays only when every pair

@@ -4,11 +4,15 @@
 // arrival order while the job-state bytes (sw_state_bytes) fit in the budget
 // and a slot is free, creating the job's handle from its initial condition
 // and opening its interval; (2) groups the active jobs by compatible block
-// shapes and stepper (all grids 64..512 together, every other size on its
-// own; one stepper per group) and
-// advances each group as one sw_batch by the largest step count no member
-// overshoots (at most chunk_steps); (3) completes the jobs whose interval has
-// ended: lmean_end into the caller's host buffers, handle released.
+// shapes and stepper (all grids 64..512 together, every larger size in a
+// group of its own size; one stepper per group) and advances each group as
+// one sw_batch by the largest step count no member overshoots (at most
+// chunk_steps); (3) completes the jobs whose interval has ended: lmean_end
+// into the caller's host buffers, handle released.
+// Without a caller stream every group has a stream of its own (its jobs'
+// handles are created on it), so the groups' steps overlap on the device: a
+// 2048^2 group and a batch of small grids run side by side.  Steps are
+// enqueued asynchronously; the loop waits only when it completes a job.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,8 +55,8 @@ int group_key(const sw_params& p) { return ((p.N >= 64 && p.N <= 512) ? 0 : p.N)
 struct sw_server {
   sw_server_params p{};
   int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
+  cudaStream_t stream = nullptr;  // the caller's stream for every group, or null
+  std::map<int, cudaStream_t> gstreams;  // per group key, without a caller stream
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -114,7 +118,22 @@ struct sw_server {
         st.peak_bytes = std::max(st.peak_bytes, st.bytes_in_use);
       }
       jb.t_admit = now();
-      int rc = sw_create(&jb.j.params, jb.j.ic_uvh, 0, stream, &jb.h);
+      cudaStream_t js = stream;
+      int rc = SW_OK;
+      if (!js) {
+        auto it = gstreams.find(group_key(jb.j.params));
+        if (it == gstreams.end()) {
+          cudaStream_t ns = nullptr;
+          if (cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            rc = SW_ECUDA;
+          } else {
+            it = gstreams.emplace(group_key(jb.j.params), ns).first;
+          }
+        }
+        if (rc == SW_OK) js = it->second;
+      }
+      if (rc == SW_OK) rc = sw_create(&jb.j.params, jb.j.ic_uvh, 0, js, &jb.h);
       if (rc == SW_OK) rc = lmean_begin(jb.h, &jb.j.lm);
       if (rc != SW_OK) {
         if (jb.h) sw_destroy(jb.h);
@@ -128,22 +147,22 @@ struct sw_server {
     }
   }
 
-  // (re)build the batch groups when membership changed
+  // (re)build the batch groups whose membership changed (a batch must be
+  // destroyed before any of its members; destroying it waits for its stream)
   int regroup() {
     std::map<int, std::vector<sw_handle*>> want;
     for (auto& jb : active) want[group_key(jb.j.params)].push_back(jb.h);
-    bool same = want.size() == groups.size();
-    if (same)
-      for (auto& kv : want) {
-        auto it = groups.find(kv.first);
-        if (it == groups.end() || it->second.members != kv.second) {
-          same = false;
-          break;
-        }
+    for (auto it = groups.begin(); it != groups.end();) {
+      auto w = want.find(it->first);
+      if (w == want.end() || w->second != it->second.members) {
+        if (it->second.batch) sw_batch_destroy(it->second.batch);
+        it = groups.erase(it);
+      } else {
+        ++it;
       }
-    if (same) return SW_OK;
-    drop_groups();
+    }
     for (auto& kv : want) {
+      if (groups.count(kv.first)) continue;
       Group g;
       g.members = kv.second;
       int rc = sw_batch_create(g.members.data(), (int)g.members.size(), &g.batch);
@@ -151,6 +170,17 @@ struct sw_server {
       groups[kv.first] = g;
     }
     return SW_OK;
+  }
+
+  // destroy the batch that holds handle h (before h itself is destroyed)
+  void drop_group_of(sw_handle* h) {
+    for (auto it = groups.begin(); it != groups.end(); ++it)
+      for (sw_handle* m : it->second.members)
+        if (m == h) {
+          if (it->second.batch) sw_batch_destroy(it->second.batch);
+          groups.erase(it);
+          return;
+        }
   }
 
   void round() {
@@ -190,8 +220,9 @@ struct sw_server {
       Job fin = jb;
       active.erase(active.begin() + i);
       set_active_count();
-      // the batch that holds this handle must go before the handle
-      drop_groups();
+      // the batch that holds this handle must go before the handle; the
+      // other groups keep their batches and their work in flight
+      drop_group_of(fin.h);
       sw_destroy(fin.h);
       finish(fin, rc);
     }
@@ -214,6 +245,8 @@ struct sw_server {
     for (auto& jb : active)
       if (jb.h) sw_destroy(jb.h);
     active.clear();
+    for (auto& kv : gstreams) cudaStreamDestroy(kv.second);
+    gstreams.clear();
   }
 };
 
@@ -230,12 +263,7 @@ extern "C" int sw_server_create(const sw_server_params* p, sw_server** out) {
   s->p = *p;
   s->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&s->device);
-  if (e == cudaSuccess && !p->stream) {
-    e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    s->own_stream = e == cudaSuccess;
-  } else {
-    s->stream = (cudaStream_t)p->stream;
-  }
+  s->stream = (cudaStream_t)p->stream;
   if (e != cudaSuccess) {
     lm::set_handleless_error(std::string("sw_server_create: ") + cudaGetErrorString(e));
     delete s;
@@ -296,6 +324,5 @@ extern "C" void sw_server_destroy(sw_server* s) {
   }
   s->cv_work.notify_all();
   if (s->th.joinable()) s->th.join();
-  if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
 }

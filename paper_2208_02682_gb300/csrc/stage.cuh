@@ -83,11 +83,15 @@ __device__ __forceinline__ const cplx<T>* stage_input(const RunDesc<T>& d, int s
 // C-wide contiguous runs of the kx-major fields straight from and to
 // registers.  Smem: C * col_buf_stride(N, C) complex.
 
+// Threads per column-pass block at most: C*N/8 is 256 up to 512^2 and in
+// FP64; FP32 tiles of 4 columns at 1024^2 and 2048^2 take 512 and 1024.
+template <typename T> constexpr int col_max_threads() { return sizeof(T) == 4 ? 1024 : 256; }
+
 // a1: column inverse pass, local block = (output field, kx tile):
 // mixed = IFFT_y(op(spectral)) with op in {id, d_x, d_y, curl}, zero-padded
 // outside |ky| <= K.
 template <typename T>
-__global__ void __launch_bounds__(256) k_stage_col_inv(const RunDesc<T>* __restrict__ runs,
+__global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_inv(const RunDesc<T>* __restrict__ runs,
                                                        const int* __restrict__ start, int nruns, int stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(256) k_stage_col_inv(const RunDesc<T>* __restr
 // (product, kx tile): spectral = FFT_y(mixed)/N on the rows |ky| <= K (zero
 // for kx > K).
 template <typename T>
-__global__ void __launch_bounds__(256) k_stage_col_fwd(const RunDesc<T>* __restrict__ runs,
+__global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_fwd(const RunDesc<T>* __restrict__ runs,
                                                        const int* __restrict__ start, int nruns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = find_run(start, nruns, blockIdx.x);
@@ -232,20 +236,28 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 // pairs in turn.  Wp > 1 only when a group is a whole
 // number of warps (N >= 256), so groups that do different numbers of
 // transforms never share a warp barrier.
+// Products are formed in the registers that feed the forward transform of
+// their pair: a pair holds at most one product that needs a transform or a
+// gather of its own ("heavy", placed first) unless Layout.heavy2 says
+// otherwise, so the first product overwrites its gradient pair element by
+// element and the second is formed from the base fields beside it.
 // Smem: per row U (u, v, h, zeta and, Strategy 2, xi_x, xi_y: N reals each);
-// per group two exchange buffers of row_stride(N) complex, PZ (the two
-// products of a pair) and, Strategy 2, S (the first product's gathered
-// values; the second's are gathered into its PZ row), N reals each.
+// per group two exchange buffers of row_stride(N) complex and
+// row_prod_group_rows(L) rows of N reals: Strategy 2, the first product's
+// values gathered at x + xi; with heavy2, the first product's values while
+// the second is transformed and (Strategy 2) the second product's gathered
+// values.
 
 // Threads per row-pass block at most (two blocks per SM: up to 85 registers
 // in FP32, 128 in FP64).
 template <typename T> constexpr int row_prod_max_threads() { return sizeof(T) == 4 ? 384 : 256; }
 
-// Rows of N reals per group of the row pass besides its exchange buffers:
-// the pair's two products and, Strategy 2, the values gathered at x + xi for
-// the first product (the second product's are gathered into its own row,
-// which the product then overwrites element by element).
-__host__ __device__ __forceinline__ int row_prod_group_rows(int strategy, int) { return strategy == 2 ? 3 : 2; }
+__device__ __forceinline__ bool product_heavy(int k) { return k == PK_ADV || k == PK_XI || k == PK_GBAR; }
+
+// Rows of N reals per group of the row pass besides its exchange buffers.
+__host__ __device__ __forceinline__ int row_prod_group_rows(const Layout& L) {
+  return (L.strategy == 2 ? 1 : 0) + (L.heavy2 ? (L.strategy == 2 ? 2 : 1) : 0);
+}
 
 template <typename T, bool WARP>
 __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod(const RunDesc<T>* __restrict__ runs,
@@ -266,14 +278,15 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const int y = rb * B + row;
   const int rs = row_stride<T>(N);
   const bool s2 = L.strategy == 2;
-  const int nur = s2 ? 6 : 4, nug = row_prod_group_rows(L.strategy, N);
+  const int nur = s2 ? 6 : 4, nug = row_prod_group_rows(L);
   T* U = reinterpret_cast<T*>(smem_raw) + (size_t)row * nur * N;
   T* XI = U + 4 * N;
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(reinterpret_cast<T*>(smem_raw) + (size_t)B * nur * N) +
                   (size_t)gi * (2 * rs + (nug * N) / 2);
   cplx<T>* buf1 = buf0 + rs;
-  T* PZ = reinterpret_cast<T*>(buf1 + rs);
-  T* S = PZ + 2 * N;
+  T* S0 = reinterpret_cast<T*>(buf1 + rs);  // Strategy 2: first product's gathered values
+  T* P0 = S0 + (s2 ? N : 0);                // heavy2: first product's values
+  T* S1 = P0 + N;                           // heavy2, Strategy 2: second product's gathered values
   const int np = L.np;
   const int p0 = pg * d.ppb * 2;
   const int p1 = min(np, p0 + d.ppb * 2);
@@ -319,8 +332,7 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   // base fields
   const int npair = (p1 - p0 + 1) >> 1;
   auto load_grad = [&](int p) {
-    const int k = L.pk[p];
-    if (k == PK_ADV || k == PK_XI || k == PK_GBAR)
+    if (product_heavy(L.pk[p]))
       load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
                             g.K);
   };
@@ -340,91 +352,106 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
     }
   };
 
+  // product p at the thread's positions into the real (slot 0) or imaginary
+  // (slot 1) parts of x; a heavy product reads its gradient pair from x at
+  // the same position first, and (Strategy 2) its gathered values from sv
+  auto form = [&](int p, int slot, const T* sv) {
+    const int kind = L.pk[p], pc = L.pc[p];
+    auto put = [&](int m, T v) {
+      if (slot) x[m].y = v;
+      else x[m].x = v;
+    };
+    switch (kind) {
+      case PK_ZV:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[N + m * G + j]);
+        break;
+      case PK_ZU:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[m * G + j]);
+        break;
+      case PK_KE:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T u = U[m * G + j], v = U[N + m * G + j];
+          put(m, (T)0.5 * (u * u + v * v));
+        }
+        break;
+      // depth h = 1 + eta; the state and the row buffers hold eta
+      case PK_HU:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T u = U[m * G + j];
+          put(m, u + U[2 * N + m * G + j] * u);
+        }
+        break;
+      case PK_HV:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T v = U[N + m * G + j];
+          put(m, v + U[2 * N + m * G + j] * v);
+        }
+        break;
+      case PK_Q:
+#pragma unroll
+        for (int m = 0; m < 8; ++m) put(m, (f0 + U[3 * N + m * G + j]) / ((T)1 + U[2 * N + m * G + j]));
+        break;
+      case PK_ADV:
+        // u.grad G (Eq. gtilde-evol) or u.grad D
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const T ua = kin ? adv_x : U[m * G + j], va = kin ? adv_y : U[N + m * G + j];
+          put(m, ua * x[m].x + va * x[m].y);
+        }
+        break;
+      default: {
+        // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int e = m * G + j;
+          const T xx = XI[e], xy = XI[N + e];
+          const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
+          const bool sz = s0 && !(xf && kind == PK_GBAR);
+          const T is = kind == PK_GBAR ? inv_sg : inv_s;
+          const T wx = sz ? (T)0.5 * ua : xx * is;
+          const T wy = sz ? (T)0.5 * va : xy * is;
+          const T wgrad = wx * x[m].x + wy * x[m].y;
+          const T fi = (kind == PK_XI && kin) ? (pc == 0 ? adv_x : adv_y) : sv[e];
+          put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wgrad : fi - wgrad);
+        }
+        break;
+      }
+    }
+  };
+
   // product pairs, shared out over the row's groups
   for (int q = wg; q < npair; q += W) {
     const int pa = p0 + 2 * q;
     const int npq = min(2, p1 - pa);
+    const bool h2 = npq == 2 && product_heavy(L.pk[pa + 1]);
     if (q != wg) load_grad(pa);
     if (s2) {
-      // both products' gathers, issued together
-      gather(pa, S);
-      if (npq == 2) gather(pa + 1, PZ + N);
+      // both products' gathers, issued together ahead of the transforms
+      gather(pa, S0);
+      if (h2) gather(pa + 1, S1);
     }
-    for (int slot = 0; slot < npq; ++slot) {
-      const int p = pa + slot;
-      const int kind = L.pk[p];
-      if (slot == 1) load_grad(p);
-      if (kind == PK_ADV || kind == PK_XI || kind == PK_GBAR) {
-        group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
-      }
-      const int pc = L.pc[p];
-      T* const pz = PZ + slot * N;
-      auto put = [&](int m, T v) { pz[m * G + j] = v; };
-      switch (kind) {
-        case PK_ZV:
+    if (product_heavy(L.pk[pa])) group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    form(pa, 0, S0);
+    if (h2) {
+      // the second product needs its own transform: park the first
 #pragma unroll
-          for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[N + m * G + j]);
-          break;
-        case PK_ZU:
+      for (int m = 0; m < 8; ++m) P0[m * G + j] = x[m].x;
+      load_grad(pa + 1);
+      group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+      form(pa + 1, 1, S1);
 #pragma unroll
-          for (int m = 0; m < 8; ++m) put(m, U[3 * N + m * G + j] * U[m * G + j]);
-          break;
-        case PK_KE:
+      for (int m = 0; m < 8; ++m) x[m].x = P0[m * G + j];
+    } else if (npq == 2) {
+      form(pa + 1, 1, nullptr);
+    } else {
 #pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const T u = U[m * G + j], v = U[N + m * G + j];
-            put(m, (T)0.5 * (u * u + v * v));
-          }
-          break;
-        // depth h = 1 + eta; the state and the row buffers hold eta
-        case PK_HU:
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const T u = U[m * G + j];
-            put(m, u + U[2 * N + m * G + j] * u);
-          }
-          break;
-        case PK_HV:
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const T v = U[N + m * G + j];
-            put(m, v + U[2 * N + m * G + j] * v);
-          }
-          break;
-        case PK_Q:
-#pragma unroll
-          for (int m = 0; m < 8; ++m) put(m, (f0 + U[3 * N + m * G + j]) / ((T)1 + U[2 * N + m * G + j]));
-          break;
-        case PK_ADV:
-          // u.grad G (Eq. gtilde-evol) or u.grad D
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const T ua = kin ? adv_x : U[m * G + j], va = kin ? adv_y : U[N + m * G + j];
-            put(m, ua * x[m].x + va * x[m].y);
-          }
-          break;
-        default: {
-          // Strategy 2, Eqs. (xi_evol), (barf_xi): w = xi/s, limit u/2 at s = 0
-          const T* const sv = slot == 0 ? S : PZ + N;
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const int e = m * G + j;
-            const T xx = XI[e], xy = XI[N + e];
-            const T ua = kin ? adv_x : U[e], va = kin ? adv_y : U[N + e];
-            const bool sz = s0 && !(xf && kind == PK_GBAR);
-            const T is = kind == PK_GBAR ? inv_sg : inv_s;
-            const T wx = sz ? (T)0.5 * ua : xx * is;
-            const T wy = sz ? (T)0.5 * va : xy * is;
-            const T wgrad = wx * x[m].x + wy * x[m].y;
-            const T fi = (kind == PK_XI && kin) ? (pc == 0 ? adv_x : adv_y) : sv[e];
-            put(m, kind == PK_XI ? fi - (pc == 0 ? wx : wy) - wgrad : fi - wgrad);
-          }
-          break;
-        }
-      }
+      for (int m = 0; m < 8; ++m) x[m].y = (T)0;
     }
-#pragma unroll
-    for (int m = 0; m < 8; ++m) x[m] = mk<T>(PZ[m * G + j], npq == 2 ? PZ[N + m * G + j] : (T)0);
     group_fft<T, -1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
     store_pair_spectrum<T, WARP>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
                            npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, G, gi, N, g.K,
@@ -469,23 +496,25 @@ __device__ __forceinline__ void slave_velocity(cplx<T>* b, const Layout& L, long
   b[L.f_v * ms + m] = mk<T>(kxf * z.y * inv, -kxf * z.x * inv);
 }
 
-// y_{n+1} = E^2 y_n + inc at element o of field f (compensated in FP32 for
-// the fields marked so).
+// y_{n+1} = E^2 y_n + inc at element o of field f, with the factor E^2 given
+// as the unevaluated sum e2h + e2l (the part e2l y_n joins the increment);
+// compensated in FP32 for the fields marked so.
 template <typename T>
-__device__ __forceinline__ void commit_mode(const RunDesc<T>& d, int f, long long o, T E, cplx<T> inc) {
+__device__ __forceinline__ void commit_mode(const RunDesc<T>& d, int f, long long o, T e2h, T e2l, cplx<T> inc) {
   const cplx<T> yn = d.y[o];
-  const T E2 = E * E;
+  inc.x = fma(yn.x, e2l, inc.x);
+  inc.y = fma(yn.y, e2l, inc.y);
   if (d.comp && d.L.fkahan[f]) {
     cplx<T> cc = d.comp[o];
-    cc.x *= E2;
-    cc.y *= E2;
+    cc.x *= e2h;
+    cc.y *= e2h;
     cplx<T> out;
-    out.x = kahan_add_rn(yn.x * E2, inc.x, cc.x);
-    out.y = kahan_add_rn(yn.y * E2, inc.y, cc.y);
+    out.x = kahan_add_rn(yn.x * e2h, inc.x, cc.x);
+    out.y = kahan_add_rn(yn.y * e2h, inc.y, cc.y);
     d.y[o] = out;
     d.comp[o] = cc;
   } else {
-    d.y[o] = cadd<T>(cscale<T>(yn, E2), inc);
+    d.y[o] = mk<T>(fma(yn.x, e2h, inc.x), fma(yn.y, e2h, inc.y));
   }
 }
 
@@ -502,7 +531,10 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   const bool e2 = L.model == 2;
   if (e2 && (role == R_U || role == R_V)) return;
   const int cls = L.fclass[f];
-  const T E = cls == IF_NONE ? (T)1 : d.ef[cls * g.ms + m];
+  const T E = cls == IF_NONE ? (T)1 : d.ef[3 * cls * g.ms + m];
+  // E^2 = e2h + e2l for the commit of y_{n+1} (read where it is committed)
+  auto e2h = [&]() { return cls == IF_NONE ? (T)1 : d.ef[(3 * cls + 1) * g.ms + m]; };
+  auto e2l = [&]() { return cls == IF_NONE ? (T)0 : d.ef[(3 * cls + 2) * g.ms + m]; };
   const long long o = f * g.ms + m;
   const T kxf = (T)kx, kyf = (T)(kyi - g.K);
   // xi-first scheme (Strategy 2, forward Euler): xi steps by 2 dt on even
@@ -513,7 +545,15 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   if (st == 2 && stage == 1) {
     // forward Euler, second pass: y_{n+1} = E^2 y_n + dt E^2 a, the increment
     // from the first pass (a separate pass: the first reads other fields' y_n)
-    commit_mode<T>(d, f, o, x1 ? E * E : E, d.acc[o]);
+    const T h2 = e2h(), l2 = e2l();
+    if (x1) {
+      // E^4 = (h2 + l2)^2 to the same precision (exact product of h2 by fma)
+      const T e4h = h2 * h2;
+      const T e4l = fma(h2, h2, -e4h) + (T)2 * h2 * l2;
+      commit_mode<T>(d, f, o, e4h, e4l, d.acc[o]);
+    } else {
+      commit_mode<T>(d, f, o, h2, l2, d.acc[o]);
+    }
     if (e2 && role == R_H) slave_velocity<T>(d.y, L, g.ms, m, kxf, kyf);
     return;
   }
@@ -597,7 +637,7 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
   } else {
     // final stage: y_{n+1} = E^2 y_n + inc, with inc = dt/6 (acc + d) (RK4)
     // or dt/2 (acc + b) (Heun); its inputs are the stage buffers, not y
-    commit_mode<T>(d, f, o, E, cscale<T>(cadd<T>(d.acc[o], rhs), st == 0 ? dt / (T)6 : dt / (T)2));
+    commit_mode<T>(d, f, o, e2h(), e2l(), cscale<T>(cadd<T>(d.acc[o], rhs), st == 0 ? dt / (T)6 : dt / (T)2));
   }
   if (e2 && role == R_H && st != 2) slave_velocity<T>(last ? d.y : yout, L, g.ms, m, kxf, kyf);
 }

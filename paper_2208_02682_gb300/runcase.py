@@ -34,6 +34,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1003)
     ap.add_argument("--cufft", action="store_true",
                     help="also time cuFFT (torch.fft) on the same transform counts, for comparison")
+    ap.add_argument("--shapes", action="store_true",
+                    help="also time the step under every row-pass launch shape the grid admits "
+                         "(sw_batch_set_shape on a batch of one)")
     args = ap.parse_args(argv)
 
     import torch
@@ -61,6 +64,32 @@ def main(argv=None):
     torch.cuda.synchronize()
     graph_ms = e0.elapsed_time(e1) / max(1, args.graph_steps)
     kt = lm.sw_kernel_times(h, args.steps)
+    shapes = None
+    if args.shapes:
+        # graph replays of a batch of one under each shape, each on a fresh
+        # interval (the first half untimed: a new graph's first replay uploads it)
+        if args.strategy:
+            lm.lmean_end(h, {})
+        shapes = {}
+        b = lm.sw_batch_create([h])
+        reps = max(2, args.graph_steps // 2)
+        for c in range(16):
+            pts = (256, 512, 1024, 2048)[c // 4]
+            if pts < N:
+                continue
+            lm.sw_batch_set_shape(b, c)
+            if args.strategy:
+                lm.lmean_begin(h, lm.make_lm_params(args.strategy, fields, n_steps=2 * reps))
+            lm.sw_batch_step(b, reps)
+            torch.cuda.synchronize()
+            e0.record()
+            lm.sw_batch_step(b, reps)
+            e1.record()
+            torch.cuda.synchronize()
+            shapes[f"{pts}pts_{(1, 2, 3, 'all')[c % 4]}pairs"] = e0.elapsed_time(e1) / reps
+            if args.strategy:
+                lm.lmean_end(h, {})
+        lm.sw_batch_destroy(b)
     lm.sw_destroy(h)
     tot = sum(v[0] for v in kt.values())
     out = {
@@ -71,6 +100,8 @@ def main(argv=None):
                         "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9}
                     for k, (t, c, b) in sorted(kt.items(), key=lambda kv: -kv[1][0])},
     }
+    if shapes is not None:
+        out["step_ms_by_row_pass_shape"] = shapes
     if args.cufft:
         out["cufft_comparison"] = cufft_reference(torch, N, args.precision, kt)
     print(json.dumps(out))

@@ -1,5 +1,7 @@
 """Serving: continuous batching under an HBM budget.  Jobs that arrive while
-others run are admitted as memory frees up, share batched launches, and each
+others run are admitted as memory frees up, share batched launches (grids
+64..512 in one group, each larger size in a group of its own: two 2048^2 and
+two 1024^2 jobs here), the groups step on streams of their own, and each
 result is the same (bit for bit) as the job run alone."""
 import time
 
@@ -19,6 +21,9 @@ JOBS = [
     (512, 1, ("zeta",), 12),
     (1024, 2, ("h",), 6),
     (128, 1, ("zeta", "h", "u", "v", "q"), 30),
+    (2048, 1, ("zeta", "h"), 5),
+    (1024, 1, ("v",), 7),
+    (2048, 2, ("u",), 4),
 ]
 
 
@@ -29,7 +34,7 @@ def lm():
 
 def _params(lm, N):
     K = (N - 1) // 3
-    return lm.make_params(N, 5e-3, precision="f32", nu8=10.0 / K ** 8)
+    return lm.make_params(N, 5e-3 if N <= 1024 else 2e-3, precision="f32", nu8=10.0 / K ** 8)
 
 
 def _outputs(N, strat, fields):
