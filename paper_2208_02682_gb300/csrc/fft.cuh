@@ -281,6 +281,148 @@ __device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
   w ^= 1;
 }
 
+// ---------------------------------------------------------------------------
+// Group transforms with the length fixed at compile time: N = 2^L, G = N/8
+// threads per transform, the same passes, data placement and arithmetic as
+// group_fft (thread j holds positions j + m G on entry and on exit), but
+// every stride, shared-memory offset and twiddle-table offset is a
+// compile-time constant: with run-time lengths the index arithmetic cost
+// more instructions than the butterflies.  Twiddles are applied without a
+// branch at k = 0 (the table holds w^0 = 1 there; the product is exact).
+// SYNC: 0 the warp (G <= 32), 1 named barrier grp + 1 over the group's G
+// threads, 2 the block (groups whose threads interleave, column tiles).
+
+template <int SYNC, int G>
+__device__ __forceinline__ void gsync(int grp) {
+  if (SYNC == 2) __syncthreads();
+  else if (SYNC == 1) asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(G) : "memory");
+  else __syncwarp();
+}
+
+// Twiddles w^{r k}, 1 <= r < R, of a butterfly of the pass with stride
+// Ns = 2^LNS (see butterfly_twiddles).
+template <typename T, int SIGN, int R, int LNS, bool TWC>
+__device__ __forceinline__ void twiddles_ct(cplx<T>* w, int k, const cplx<T>* __restrict__ tw) {
+  constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  const cplx<T>* t = tw + (k - 1);
+  if (sizeof(T) == 4) {
+    auto ev = [&](int r) {
+      cplx<T> c;
+      if (TWC) {
+        float sn, cs;
+        // 2 r k / (Ns R), exact in FP32 (a power-of-two scale)
+        sincospif((float)(r * k) * (2.0f / (float)(1 << (LNS + LR))), &sn, &cs);
+        c.x = (T)cs;
+        c.y = (T)(-sn);
+      } else {
+        c = __ldg(t + (r << LNS));
+      }
+      if (SIGN > 0) c.y = -c.y;
+      return c;
+    };
+    w[1] = ev(1);
+    if (R >= 4) {
+      w[2] = ev(2);
+      w[3] = cmul<T>(w[1], w[2]);
+    }
+    if (R == 8) {
+      w[4] = ev(4);
+      w[5] = cmul<T>(w[4], w[1]);
+      w[6] = cmul<T>(w[4], w[2]);
+      w[7] = cmul<T>(w[4], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      w[r] = __ldg(t + (r << LNS));
+      if (SIGN > 0) w[r].y = -w[r].y;
+    }
+  }
+}
+
+// Middle pass P (radix 8, stride Ns = 8^P) from `in` to `out`.
+template <typename T, int SIGN, int L, int P, bool TWC>
+__device__ __forceinline__ void gpass8(const cplx<T>* in, cplx<T>* out, int j, const cplx<T>* __restrict__ tw) {
+  constexpr int G = 1 << (L - 3), LNS = 3 * P, NS = 1 << LNS;
+  constexpr int RS = G + G / 8;    // shared-memory distance of G positions (G % 8 == 0)
+  constexpr int WS = NS + NS / 8;  // of Ns positions
+  cplx<T> v[8];
+  const int rb = j + (j >> 3);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = in[rb + r * RS];
+  const int k = j & (NS - 1);
+  cplx<T> wr[8];
+  twiddles_ct<T, SIGN, 8, LNS, TWC>(wr, k, tw);
+#pragma unroll
+  for (int r = 1; r < 8; ++r) v[r] = cmul<T>(v[r], wr[r]);
+  dft8<T, SIGN>(v);
+  const int o = ((j - k) << 3) + k;
+  const int ob = o + (o >> 3);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[ob + q * WS] = v[q];
+}
+
+// Last pass (radix 8, 4 or 2) from `in` into the registers x.
+template <typename T, int SIGN, int L, bool TWC>
+__device__ __forceinline__ void gpass_last(cplx<T> (&x)[8], const cplx<T>* in, int j,
+                                           const cplx<T>* __restrict__ tw) {
+  constexpr int G = 1 << (L - 3), NP = (L + 2) / 3, P = NP - 1;
+  constexpr int LNS = 3 * P, NS = 1 << LNS, LR = L - LNS, R = 1 << LR, NB = 8 / R;
+  constexpr int RS = (G * NB) + (G * NB) / 8;  // distance of N/R positions (a multiple of 8)
+  cplx<T> v[8];
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int jj = u * G + j;
+    const int k = jj & (NS - 1);
+    const int rb = jj + (jj >> 3);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[u * R + r] = in[rb + r * RS];
+    cplx<T> wr[8];
+    twiddles_ct<T, SIGN, R, LNS, TWC>(wr, k, tw);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], wr[r]);
+  }
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    dft_r<T, SIGN, R>(v + u * R);
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[u + q * NB] = v[u * R + q];
+  }
+}
+
+template <typename T, int SIGN, int L, int P, int SYNC, bool TWC>
+__device__ __forceinline__ void gpass_mid(cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int grp,
+                                          const cplx<T>* __restrict__ tw) {
+  constexpr int NP = (L + 2) / 3;
+  if constexpr (P < NP - 1) {
+    gpass8<T, SIGN, L, P, TWC>(w ? buf1 : buf0, w ? buf0 : buf1, j, tw);
+    gsync<SYNC, (1 << (L - 3))>(grp);
+    w ^= 1;
+    gpass_mid<T, SIGN, L, P + 1, SYNC, TWC>(buf0, buf1, w, j, grp, tw);
+  }
+}
+
+// The transform of x (positions j + m G in, positions j + m G out); w selects
+// the exchange buffer that is free to write and is left pointing at the
+// buffer not read last (as group_fft).
+template <typename T, int SIGN, int L, int SYNC, bool TWC>
+__device__ __forceinline__ void gfft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int grp,
+                                     const cplx<T>* __restrict__ tw) {
+  static_assert(L >= 4 && L <= 11, "transform length 16..2048");
+  constexpr int G = 1 << (L - 3);
+  dft8<T, SIGN>(x);
+  {
+    cplx<T>* out = w ? buf1 : buf0;
+    const int b = 9 * j;  // sidx(8 j + q) = 9 j + q
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[b + q] = x[q];
+  }
+  gsync<SYNC, G>(grp);
+  gpass_mid<T, SIGN, L, 1, SYNC, TWC>(buf0, buf1, w, j, grp, tw);
+  gpass_last<T, SIGN, L, TWC>(x, w ? buf1 : buf0, j, tw);
+  w ^= 1;
+}
+
 // Host: the pass-ordered twiddle table of an N-point transform (N - 1
 // entries, FP64).
 inline void fft_twiddle_table(int log2N, double* re, double* im) {

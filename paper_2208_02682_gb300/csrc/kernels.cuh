@@ -246,6 +246,77 @@ __device__ __forceinline__ void store_pair_spectrum(const cplx<T> (&x)[8], cplx<
   w ^= 1;
 }
 
+// The same two row helpers with the length N = 2^L fixed at compile time
+// (G = N/8), for the stage kernels' specialised bodies.
+template <typename T, int L>
+__device__ __forceinline__ void load_pair_spectrum_ct(cplx<T> (&x)[8], const cplx<T>* __restrict__ ma,
+                                                      const cplx<T>* __restrict__ mb, long long rowoff, int j,
+                                                      int K) {
+  constexpr int N = 1 << L, G = N / 8;
+  const cplx<T>* ra = ma + rowoff;
+  const cplx<T>* rb = mb ? mb + rowoff : nullptr;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = j + m * G;
+    cplx<T> z = mk<T>(0, 0);
+    if (k <= K) {
+      const cplx<T> A = ra[k];
+      const cplx<T> Bv = rb ? rb[k] : mk<T>(0, 0);
+      z = k == 0 ? mk<T>(A.x, Bv.x) : mk<T>(A.x - Bv.y, A.y + Bv.x);
+    } else if (k >= N - K) {
+      const cplx<T> A = ra[N - k];
+      const cplx<T> Bv = rb ? rb[N - k] : mk<T>(0, 0);
+      z = mk<T>(A.x + Bv.y, -A.y + Bv.x);
+    }
+    x[m] = z;
+  }
+}
+
+template <typename T, int L, int SYNC>
+__device__ __forceinline__ void store_pair_spectrum_ct(const cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
+                                                       cplx<T>* __restrict__ da, cplx<T>* __restrict__ db,
+                                                       long long rowoff, int j, int grp, int K, int KXP) {
+  constexpr int N = 1 << L, G = N / 8;
+  cplx<T>* b = w ? buf1 : buf0;
+  if constexpr (G % 8 == 0) {
+    const int sb = j + (j >> 3);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) b[sb + m * (G + G / 8)] = x[m];  // sidx(j + m G)
+  } else {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) b[sidx<T>(j + m * G)] = x[m];
+  }
+  gsync<SYNC, G>(grp);
+  const T h = (T)0.5 / (T)N;
+  cplx<T>* ra = da + rowoff;
+  cplx<T>* rb = db ? db + rowoff : nullptr;
+  for (int k = j; k < KXP; k += G) {
+    cplx<T> P = mk<T>(0, 0), Q = mk<T>(0, 0);
+    if (k <= K) {
+      const cplx<T> z1 = b[k + (k >> 3)];
+      const int k2 = (N - k) & (N - 1);
+      const cplx<T> z2 = b[k2 + (k2 >> 3)];
+      // P = (Z(k) + conj Z(N-k))/2, Q = (Z(k) - conj Z(N-k))/(2i)
+      P = mk<T>((z1.x + z2.x) * h, (z1.y - z2.y) * h);
+      Q = mk<T>((z1.y + z2.y) * h, (z2.x - z1.x) * h);
+    }
+    ra[k] = P;
+    if (rb) rb[k] = Q;
+  }
+  w ^= 1;
+}
+
+// Call f(IntC<L>()) for the run-time length exponent L in [LO, HI]: the
+// stage kernels' bodies are compiled once per transform length.
+template <int V> struct IntC { static constexpr int value = V; };
+template <int LO, int HI, typename F>
+__device__ __forceinline__ void dispatch_L(int L, F&& f) {
+  if constexpr (LO <= HI) {
+    if (L == LO) f(IntC<LO>());
+    else dispatch_L<LO + 1, HI>(L, f);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Row pass, inverse: physical outputs from pairs of mixed fields, with an
 // affine epilogue out = scale*val + ax*x + ay*y + c (mean positions; the

@@ -97,40 +97,53 @@ __global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_inv(const Ru
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   pdl_wait();  // state written by the previous kernels: only after this
-  const Geom& g = d.g;
-  const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
-  const int lC = d.lC, C = 1 << lC;
   const int lb = blockIdx.x - start[r];
-  const int ntile = KXP >> lC;
-  const int o = lb / ntile, tile = lb - o * ntile;
-  const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
-  const int kx = (tile << lC) + c;
-  const cplx<T>* src = stage_input(d, stage);
-  const int op = d.L.i_op[o];
-  const cplx<T>* s1 = src + (long long)d.L.i_src[o] * g.ms;
-  const cplx<T>* s2 = src + (long long)(d.L.i_src2[o] < 0 ? d.L.i_src[o] : d.L.i_src2[o]) * g.ms;
-  cplx<T> x[8];
+  dispatch_L<4, 11>(d.g.log2N, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value, N = 1 << L, G = N / 8;
+    const int K = d.g.K, KXP = d.g.KXP;
+    const int lC = d.lC, C = 1 << lC;
+    const int ntile = KXP >> lC;
+    const int o = lb / ntile, tile = lb - o * ntile;
+    const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
+    const int kx = (tile << lC) + c;
+    const cplx<T>* src = stage_input(d, stage);
+    const int op = d.L.i_op[o];
+    const cplx<T>* s1 = src + (long long)d.L.i_src[o] * d.g.ms + kx;
+    const cplx<T>* s2 = src + (long long)(d.L.i_src2[o] < 0 ? d.L.i_src[o] : d.L.i_src2[o]) * d.g.ms + kx;
+    const bool col = kx <= K;
+    cplx<T> x[8];
+    int kyv[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int n = j + m * G;
-    const int ky = n <= K ? n : n - N;
-    cplx<T> v = mk<T>(0, 0);
-    if (kx <= K && (n <= K || n >= N - K)) {
-      const long long mm = (long long)(ky + K) * KXP + kx;
-      const cplx<T> a = s1[mm];
-      if (op == OP_ID) v = a;
-      else if (op == OP_DX) v = cik<T>(a, (T)kx);
-      else if (op == OP_DY) v = cik<T>(a, (T)ky);
-      else v = csub<T>(cik<T>(s2[mm], (T)kx), cik<T>(a, (T)ky));  // curl: i kx v - i ky u
+    for (int m = 0; m < 8; ++m) {
+      const int n = j + m * G;
+      kyv[m] = n <= K ? n : n - N;
+      x[m] = mk<T>(0, 0);
+      if (col && (n <= K || n >= N - K)) x[m] = s1[(kyv[m] + K) * KXP];
     }
-    x[m] = v;
-  }
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
-  int w = 0;
-  group_fft<T, +1, true, true>(x, b0, b0 + col_stride<T>(N, C), w, j, G, 0, g.log2N, d.tw);
-  cplx<T>* dst = d.mix + (long long)o * g.mi + kx;
+    // the operator is uniform over the block
+    if (op == OP_DX) {
 #pragma unroll
-  for (int m = 0; m < 8; ++m) dst[(long long)(j + m * G) * KXP] = x[m];
+      for (int m = 0; m < 8; ++m) x[m] = cik<T>(x[m], (T)kx);
+    } else if (op == OP_DY) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) x[m] = cik<T>(x[m], (T)kyv[m]);
+    } else if (op == OP_CURL) {
+      // curl: i kx v - i ky u (s1 = u, s2 = v)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int n = j + m * G;
+        cplx<T> b = mk<T>(0, 0);
+        if (col && (n <= K || n >= N - K)) b = s2[(kyv[m] + K) * KXP];
+        x[m] = csub<T>(cik<T>(b, (T)kx), cik<T>(x[m], (T)kyv[m]));
+      }
+    }
+    cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
+    int w = 0;
+    gfft<T, +1, L, 2, true>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
+    cplx<T>* dst = d.mix + (long long)o * d.g.mi + kx;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) dst[(j + m * G) * KXP] = x[m];
+  });
   pdl_release();
 }
 
@@ -144,31 +157,33 @@ __global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_fwd(const Ru
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   pdl_wait();  // state written by the previous kernels: only after this
-  const Geom& g = d.g;
-  const int N = g.N, K = g.K, KXP = g.KXP, G = N >> 3;
-  const int lC = d.lC, C = 1 << lC;
   const int lb = blockIdx.x - start[r];
-  const int ntile = KXP >> lC;
-  const int p = lb / ntile, tile = lb - p * ntile;
-  const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
-  const int kx = (tile << lC) + c;
-  const cplx<T>* src = d.pmix + (long long)p * g.mi + kx;
-  cplx<T> x[8];
+  dispatch_L<4, 11>(d.g.log2N, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value, N = 1 << L, G = N / 8;
+    const int K = d.g.K, KXP = d.g.KXP;
+    const int lC = d.lC, C = 1 << lC;
+    const int ntile = KXP >> lC;
+    const int p = lb / ntile, tile = lb - p * ntile;
+    const int c = threadIdx.x & (C - 1), j = threadIdx.x >> lC;
+    const int kx = (tile << lC) + c;
+    const cplx<T>* src = d.pmix + (long long)p * d.g.mi + kx;
+    cplx<T> x[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) x[m] = src[(long long)(j + m * G) * KXP];
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
-  int w = 0;
-  group_fft<T, -1, true, true>(x, b0, b0 + col_stride<T>(N, C), w, j, G, 0, g.log2N, d.tw);
-  const T inv = (T)1 / (T)N;
-  cplx<T>* dst = d.ps + (long long)p * g.ms + kx;
+    for (int m = 0; m < 8; ++m) x[m] = src[(j + m * G) * KXP];
+    cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
+    int w = 0;
+    gfft<T, -1, L, 2, true>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
+    const T inv = (T)1 / (T)N;
+    cplx<T>* dst = d.ps + (long long)p * d.g.ms + kx;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int k = j + m * G;
-    if (k <= K || k >= N - K) {
-      const int ky = k <= K ? k : k - N;
-      dst[(long long)(ky + K) * KXP] = kx <= K ? cscale<T>(x[m], inv) : mk<T>(0, 0);
+    for (int m = 0; m < 8; ++m) {
+      const int k = j + m * G;
+      if (k <= K || k >= N - K) {
+        const int ky = k <= K ? k : k - N;
+        dst[(ky + K) * KXP] = kx <= K ? cscale<T>(x[m], inv) : mk<T>(0, 0);
+      }
     }
-  }
+  });
   pdl_release();
 }
 
@@ -181,32 +196,39 @@ __global__ void __launch_bounds__(256) k_stage_row_inv(const RunDesc<T>* __restr
   const int r = find_run(start, nruns, blockIdx.x);
   const RunDesc<T>& d = runs[r];
   pdl_wait();  // state written by the previous kernels: only after this
-  const Geom& g = d.g;
-  const int N = g.N, G = N >> 3, B = d.Bi;
   const int lb = blockIdx.x - start[r];
-  const int nrb = N / B;
-  const int pair = lb / nrb, rb = lb - pair * nrb;
-  const int grp = threadIdx.x / G, j = threadIdx.x - grp * G;
-  const int y = rb * B + grp;
-  const int rs = row_stride<T>(N);
-  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
-  cplx<T>* buf1 = buf0 + rs;
-  // pairs (u, v), (h, zeta) and, Strategy 2, (xi_x, xi_y)
-  const int ia = pair == 0 ? d.L.i_u : (pair == 1 ? d.L.i_h : d.L.i_xi[0]);
-  const int ib = pair == 0 ? d.L.i_v : (pair == 1 ? d.L.i_z : d.L.i_xi[1]);
-  const int oa = pair == 0 ? PH_U : (pair == 1 ? PH_H : PH_XX);
-  const int ob = pair == 0 ? PH_V : (pair == 1 ? PH_Z : PH_XY);
-  cplx<T> x[8];
-  int w = 0;
-  load_pair_spectrum<T>(x, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, (long long)y * g.KXP, j, G, N,
-                        g.K);
-  group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, grp, g.log2N, d.tw);
+  auto body = [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value, N = 1 << L, G = N / 8;
+    constexpr int SYNC = L <= 8 ? 0 : 1;
+    const Geom& g = d.g;
+    const int B = d.Bi;
+    const int nrb = N / B;
+    const int pair = lb / nrb, rb = lb - pair * nrb;
+    const int grp = threadIdx.x / G, j = threadIdx.x - grp * G;
+    const int y = rb * B + grp;
+    constexpr int rs = N + N / 8;
+    cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)grp * 2 * rs;
+    cplx<T>* buf1 = buf0 + rs;
+    // pairs (u, v), (h, zeta) and, Strategy 2, (xi_x, xi_y)
+    const int ia = pair == 0 ? d.L.i_u : (pair == 1 ? d.L.i_h : d.L.i_xi[0]);
+    const int ib = pair == 0 ? d.L.i_v : (pair == 1 ? d.L.i_z : d.L.i_xi[1]);
+    const int oa = pair == 0 ? PH_U : (pair == 1 ? PH_H : PH_XX);
+    const int ob = pair == 0 ? PH_V : (pair == 1 ? PH_Z : PH_XY);
+    cplx<T> x[8];
+    int w = 0;
+    load_pair_spectrum_ct<T, L>(x, d.mix + (long long)ia * g.mi, d.mix + (long long)ib * g.mi, (long long)y * g.KXP,
+                                j, g.K);
+    gfft<T, +1, L, SYNC, false>(x, buf0, buf1, w, j, grp, d.tw);
+    T* pa = d.phys + (long long)oa * g.np + (long long)y * N + j;
+    T* pb = d.phys + (long long)ob * g.np + (long long)y * N + j;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const long long off = (long long)y * N + j + m * G;
-    d.phys[oa * g.np + off] = x[m].x;
-    d.phys[ob * g.np + off] = x[m].y;
-  }
+    for (int m = 0; m < 8; ++m) {
+      pa[m * G] = x[m].x;
+      pb[m * G] = x[m].y;
+    }
+  };
+  if constexpr (WARP) dispatch_L<4, 8>(d.g.log2N, body);
+  else dispatch_L<4, 11>(d.g.log2N, body);
   pdl_release();
 }
 
@@ -267,16 +289,19 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const int r = find_run(start, nruns, blockIdx.x);
   LM_STAGE_DESC(T);  // field and product lookups from shared memory
   pdl_wait();  // state written by the previous kernels: only after this
+  const int lb = blockIdx.x - start[r];
+  auto body = [&](auto Lc) {
+  constexpr int L_ = decltype(Lc)::value, N = 1 << L_, G = N / 8;
+  constexpr int SYNC = L_ <= 8 ? 0 : 1;
   const Geom& g = d.g;
   const Layout& L = d.L;
-  const int N = g.N, B = d.Bp, W = d.Wp, G = N >> 3;
-  const int lb = blockIdx.x - start[r];
+  const int B = d.Bp, W = d.Wp;
   const int nrb = N / B;
   const int pg = lb / nrb, rb = lb - pg * nrb;
   const int gi = threadIdx.x / G, j = threadIdx.x - gi * G;
   const int row = gi / W, wg = gi - row * W;
   const int y = rb * B + row;
-  const int rs = row_stride<T>(N);
+  constexpr int rs = N + N / 8;
   const bool s2 = L.strategy == 2;
   const int nur = s2 ? 6 : 4, nug = row_prod_group_rows(L);
   T* U = reinterpret_cast<T*>(smem_raw) + (size_t)row * nur * N;
@@ -333,8 +358,8 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
   const int npair = (p1 - p0 + 1) >> 1;
   auto load_grad = [&](int p) {
     if (product_heavy(L.pk[p]))
-      load_pair_spectrum<T>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j, G, N,
-                            g.K);
+      load_pair_spectrum_ct<T, L_>(x, mix + (long long)L.pa[p] * g.mi, mix + (long long)L.pb[p] * g.mi, rowoff, j,
+                                   g.K);
   };
   if (wg < npair) load_grad(p0 + 2 * wg);
   __syncthreads();
@@ -435,14 +460,14 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
       gather(pa, S0);
       if (h2) gather(pa + 1, S1);
     }
-    if (product_heavy(L.pk[pa])) group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+    if (product_heavy(L.pk[pa])) gfft<T, +1, L_, SYNC, false>(x, buf0, buf1, w, j, gi, d.tw);
     form(pa, 0, S0);
     if (h2) {
       // the second product needs its own transform: park the first
 #pragma unroll
       for (int m = 0; m < 8; ++m) P0[m * G + j] = x[m].x;
       load_grad(pa + 1);
-      group_fft<T, +1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
+      gfft<T, +1, L_, SYNC, false>(x, buf0, buf1, w, j, gi, d.tw);
       form(pa + 1, 1, S1);
 #pragma unroll
       for (int m = 0; m < 8; ++m) x[m].x = P0[m * G + j];
@@ -452,11 +477,14 @@ __global__ void __launch_bounds__(row_prod_max_threads<T>(), 2) k_stage_row_prod
 #pragma unroll
       for (int m = 0; m < 8; ++m) x[m].y = (T)0;
     }
-    group_fft<T, -1, false, false, WARP>(x, buf0, buf1, w, j, G, gi, g.log2N, d.tw);
-    store_pair_spectrum<T, WARP>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
-                           npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, G, gi, N, g.K,
-                           g.KXP);
+    gfft<T, -1, L_, SYNC, false>(x, buf0, buf1, w, j, gi, d.tw);
+    store_pair_spectrum_ct<T, L_, SYNC>(x, buf0, buf1, w, d.pmix + (long long)pa * g.mi,
+                                        npq == 2 ? d.pmix + (long long)(pa + 1) * g.mi : nullptr, rowoff, j, gi,
+                                        g.K, g.KXP);
   }
+  };
+  if constexpr (WARP) dispatch_L<4, 8>(d.g.log2N, body);
+  else dispatch_L<4, 11>(d.g.log2N, body);
   pdl_release();
 }
 
