@@ -5,9 +5,10 @@ Used for profiling captures and quick timings of a single grid:
   python -m paper_2208_02682_gb300.runcase --N 2048 --strategy 1 --precision f32 --steps 4
 
 It creates one handle from the seeded turbulence-plus-wave initial condition,
-opens an averaging interval, replays `--graph-steps` steps from the captured
-graph (timed with CUDA events), then launches `--steps` steps kernel by
-kernel through sw_kernel_times and prints one JSON line.
+opens an averaging interval, runs one untimed step (graph capture and
+upload), replays `--graph-steps` steps from the captured graphs (timed with
+CUDA events), then launches `--steps` steps kernel by kernel through
+sw_kernel_times and prints one JSON line.
 """
 from __future__ import annotations
 
@@ -51,10 +52,11 @@ def main(argv=None):
     ic = np.ascontiguousarray(np.stack(si.turbulence_plus_waves(N, 0.05, 2.0, 8.0, 12.0, args.seed)))
     h = lm.sw_create(lm.make_params(N, dt, precision=args.precision, nu8=10.0 / K ** 8), ic)
     fields = tuple(f for f in args.fields.split(",") if f)
-    total = args.graph_steps + args.steps
+    total = 1 + args.graph_steps + args.steps
     if args.strategy:
         lm.lmean_begin(h, lm.make_lm_params(args.strategy, fields, n_steps=total))
     step = (lambda n: lm.lmean_step(h, n)) if args.strategy else (lambda n: lm.sw_step(h, n))
+    step(1)  # untimed: captures and uploads the step graphs
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
