@@ -585,7 +585,7 @@ def served_dt(N, f0=1.0, c2=1.0):
     return 5e-3 if wmax * 5e-3 <= 0.9 * 2.0 * np.sqrt(2.0) else 2.0 / wmax
 
 
-def measure_served(lm, n_jobs=40, rate=50.0, sizes=(128, 256, 512, 1024, 2048), seed=1005):
+def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024, 2048), seed=1005):
     """Poisson stream of Lagrangian-mean requests through sw_server: grids
     uniform over `sizes`, averaging windows uniform in 1-8 wave periods
     (period 2 pi/omega(|k| = 4)), strategy 1 or 2, FP32 with FP64 recovery,
@@ -867,7 +867,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, precision and served figures")
-    ap.add_argument("--serve-jobs", type=int, default=40,
+    ap.add_argument("--serve-jobs", type=int, default=24,
                     help="requests in the served stream (the full serving form is 200)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -58,7 +58,7 @@ __device__ __forceinline__ void dft8(cplx<T>* v) {
   v[3] = cadd<T>(a3, b3); v[7] = csub<T>(a3, b3);
 }
 
-// Pass sequence shared by the kernels (block_fft, group_fft) and the host
+// Pass sequence shared by the kernels (block_fft, gfft) and the host
 // table builder: radix-8 passes, then one radix-4 or radix-2 pass for the
 // remaining bits.
 __host__ __device__ __forceinline__ int fft_num_passes(int log2N) { return (log2N + 2) / 3; }
@@ -71,8 +71,9 @@ __host__ __device__ __forceinline__ int fft_pass_lr(int log2N, int p) {
 // scarce resource).  FP32 evaluates w^k, w^2k, w^4k and forms the others as
 // products (at most two multiplications deep): from the table rows r = 1, 2,
 // 4, or, with TWC, from sincospif of 2 e / (Ns R) (exact in FP32) for e = k,
-// 2k, 4k; computed twiddles suit kernels with many resident warps whose table
-// loads would queue behind shared-memory traffic.
+// 2k, 4k.  The generic column kernels compute them; the stage kernels load
+// the table (their loads stay in L1; at 1024^2-2048^2 the column passes ran
+// 10-15% faster with the table than with sincospif).
 template <typename T, int SIGN, int R, bool TWC>
 __device__ __forceinline__ void butterfly_twiddles(cplx<T>* w, int k, int lNs, const cplx<T>* __restrict__ tw) {
   constexpr int LR = R == 8 ? 3 : (R == 4 ? 2 : 1);
@@ -176,27 +177,6 @@ __device__ void block_fft(cplx<T>* buf, int log2N, int bstride, const cplx<T>* _
   if (rem == 1) stockham_pass<T, SIGN, 1, TWC>(buf, log2N, lNs, bstride, tw);
 }
 
-// ---------------------------------------------------------------------------
-// Register-resident transforms owned by a group of G = N/8 threads (one
-// transform per group; groups never wait for one another).  Thread j of the
-// group holds elements j + m G, m < 8, of its transform in x[m] on entry
-// (input) and on exit (output): the first pass's butterflies read exactly
-// these positions, and the last pass's butterflies write them.  The passes in
-// between exchange through two shared buffers used alternately, so each pass
-// costs one group barrier.  `w` selects the buffer that is free to write; the
-// function leaves it pointing at the buffer not read last.
-
-// Barrier over the group's G threads: the warp when G <= 32 (several groups
-// per warp execute the same instructions), else named barrier 1 + grp.
-// WARP: the caller guarantees G <= 32, so the kernel holds no named barrier
-// (a named barrier with a run-time id reserves all 16 of the block's
-// barriers, which limits the blocks resident on an SM).
-template <bool WARP = false>
-__device__ __forceinline__ void group_sync(int G, int grp) {
-  if (WARP || G <= 32) __syncwarp();
-  else asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(G) : "memory");
-}
-
 template <typename T, int SIGN, int R>
 __device__ __forceinline__ void dft_r(cplx<T>* v) {
   if (R == 8) {
@@ -210,87 +190,24 @@ __device__ __forceinline__ void dft_r(cplx<T>* v) {
   }
 }
 
-// One Stockham pass of a group transform, from shared memory `in` to shared
-// memory `out` (or, LAST, to the output registers x).
-template <typename T, int SIGN, int LR, bool LAST, bool TWC>
-__device__ __forceinline__ void group_pass(cplx<T>* x, const cplx<T>* in, cplx<T>* out, int j, int G, int lNs,
-                                           const cplx<T>* __restrict__ tw) {
-  constexpr int R = 1 << LR;
-  constexpr int NB = 8 / R;
-  const int NR = G * NB;
-  const int Ns = 1 << lNs;
-  cplx<T> v[8];
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    const int jj = u * G + j;
-    const int k = jj & (Ns - 1);
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[u * R + r] = in[sidx<T>(jj + r * NR)];
-    if (k > 0) {
-      cplx<T> wr[R];
-      butterfly_twiddles<T, SIGN, R, TWC>(wr, k, lNs, tw);
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[u * R + r] = cmul<T>(v[u * R + r], wr[r]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    dft_r<T, SIGN, R>(v + u * R);
-    const int jj = u * G + j;
-    const int k = jj & (Ns - 1);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      if (LAST) x[u + q * NB] = v[u * R + q];
-      else out[sidx<T>(((jj - k) << LR) + k + q * Ns)] = v[u * R + q];
-    }
-  }
-}
-
-// BLOCK: the block's transforms step together and synchronise with
-// __syncthreads (groups whose threads interleave, e.g. column tiles).
-// WARP: G <= 32 (see group_sync).
-template <typename T, int SIGN, bool TWC = false, bool BLOCK = false, bool WARP = false>
-__device__ void group_fft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int G, int grp, int log2N,
-                          const cplx<T>* __restrict__ tw) {
-  auto sync = [&]() {
-    if (BLOCK) __syncthreads();
-    else group_sync<WARP>(G, grp);
-  };
-  // first pass: radix 8, stride 1, no twiddles; butterfly j takes x[0..7]
-  dft8<T, SIGN>(x);
-  {
-    cplx<T>* out = w ? buf1 : buf0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) out[sidx<T>((j << 3) + q)] = x[q];
-  }
-  sync();
-  // radix-8 passes, then the last pass (radix 8, 4 or 2) into the registers
-  const int np = fft_num_passes(log2N);
-  int lNs = 3;
-  for (int p = 1; p < np - 1; ++p) {
-    group_pass<T, SIGN, 3, false, TWC>(x, w ? buf1 : buf0, w ? buf0 : buf1, j, G, lNs, tw);
-    sync();
-    w ^= 1;
-    lNs += 3;
-  }
-  const cplx<T>* in = w ? buf1 : buf0;
-  const int lr = fft_pass_lr(log2N, np - 1);
-  if (lr == 3) group_pass<T, SIGN, 3, true, TWC>(x, in, nullptr, j, G, lNs, tw);
-  else if (lr == 2) group_pass<T, SIGN, 2, true, TWC>(x, in, nullptr, j, G, lNs, tw);
-  else group_pass<T, SIGN, 1, true, TWC>(x, in, nullptr, j, G, lNs, tw);
-  w ^= 1;
-}
-
 // ---------------------------------------------------------------------------
-// Group transforms with the length fixed at compile time: N = 2^L, G = N/8
-// threads per transform, the same passes, data placement and arithmetic as
-// group_fft (thread j holds positions j + m G on entry and on exit), but
-// every stride, shared-memory offset and twiddle-table offset is a
-// compile-time constant: with run-time lengths the index arithmetic cost
-// more instructions than the butterflies.  Twiddles are applied without a
-// branch at k = 0 (the table holds w^0 = 1 there; the product is exact).
-// SYNC: 0 the warp (G <= 32), 1 named barrier grp + 1 over the group's G
-// threads, 2 the block (groups whose threads interleave, column tiles).
+// Register-resident transforms owned by a group of G = N/8 threads (one
+// transform per group; groups never wait for one another), N = 2^L fixed at
+// compile time.  Thread j of the group holds elements j + m G, m < 8, of its
+// transform in x[m] on entry (input) and on exit (output): the first pass's
+// butterflies read exactly these positions, and the last pass's butterflies
+// write them.  The passes in between exchange through two shared buffers
+// used alternately, so each pass costs one group barrier.  Every stride,
+// shared-memory offset and twiddle-table offset is a compile-time constant
+// (with run-time lengths the index arithmetic cost more instructions than
+// the butterflies), and twiddles are applied without a branch at k = 0 (the
+// table holds w^0 = 1 there; the product is exact).
+// SYNC: 0 the warp (G <= 32: several groups per warp execute the same
+// instructions), 1 named barrier grp + 1 over the group's G threads, 2 the
+// block (groups whose threads interleave, column tiles).  A named barrier
+// with a run-time id reserves all 16 of a block's barriers, which limits the
+// blocks resident on an SM, so kernels whose groups all fit in a warp are
+// compiled without it.
 
 template <int SYNC, int G>
 __device__ __forceinline__ void gsync(int grp) {
@@ -404,7 +321,7 @@ __device__ __forceinline__ void gpass_mid(cplx<T>* buf0, cplx<T>* buf1, int& w, 
 
 // The transform of x (positions j + m G in, positions j + m G out); w selects
 // the exchange buffer that is free to write and is left pointing at the
-// buffer not read last (as group_fft).
+// buffer not read last.
 template <typename T, int SIGN, int L, int SYNC, bool TWC>
 __device__ __forceinline__ void gfft(cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w, int j, int grp,
                                      const cplx<T>* __restrict__ tw) {

@@ -191,63 +191,13 @@ __device__ void row_pair_forward_store(cplx<T>* buf, cplx<T>* __restrict__ da,
   __syncthreads();
 }
 
-// Group-owned row transforms (one row per group of G = N/8 threads; thread
-// j holds positions j + m G, see group_fft).
+// Group-owned row transforms (one row per group of G = N/8 threads, N = 2^L
+// fixed at compile time; thread j holds positions j + m G, see gfft).
 
 // Hermitian-paired spectrum of one row of mixed fields a and b at the
 // thread's positions k = j + m G: Z(k) = A(k) + i B(k) for k <= K,
 // conj A(N-k) + i conj B(N-k) for k >= N-K, zero in between; the kx = 0
 // imaginary parts are dropped, as a real inverse transform does.
-template <typename T>
-__device__ __forceinline__ void load_pair_spectrum(cplx<T> (&x)[8], const cplx<T>* __restrict__ ma,
-                                                   const cplx<T>* __restrict__ mb, long long rowoff, int j, int G,
-                                                   int N, int K) {
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int k = j + m * G;
-    cplx<T> z = mk<T>(0, 0);
-    if (k <= K) {
-      const cplx<T> A = ma[rowoff + k];
-      const cplx<T> Bv = mb ? mb[rowoff + k] : mk<T>(0, 0);
-      z = k == 0 ? mk<T>(A.x, Bv.x) : mk<T>(A.x - Bv.y, A.y + Bv.x);
-    } else if (k >= N - K) {
-      const cplx<T> A = ma[rowoff + (N - k)];
-      const cplx<T> Bv = mb ? mb[rowoff + (N - k)] : mk<T>(0, 0);
-      z = mk<T>(A.x + Bv.y, -A.y + Bv.x);
-    }
-    x[m] = z;
-  }
-}
-
-// Spectrum Z of p + i q held at the thread's positions -> kx in [0, KXP)
-// halves of p and q, scaled by 1/N, into row `rowoff` of mixed fields da and
-// db (db null: p only).  One exchange through the free buffer.
-template <typename T, bool WARP = false>
-__device__ __forceinline__ void store_pair_spectrum(const cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
-                                                    cplx<T>* __restrict__ da, cplx<T>* __restrict__ db,
-                                                    long long rowoff, int j, int G, int grp, int N, int K, int KXP) {
-  cplx<T>* b = w ? buf1 : buf0;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) b[sidx<T>(j + m * G)] = x[m];
-  group_sync<WARP>(G, grp);
-  const T h = (T)0.5 / (T)N;
-  for (int k = j; k < KXP; k += G) {
-    cplx<T> P = mk<T>(0, 0), Q = mk<T>(0, 0);
-    if (k <= K) {
-      const cplx<T> z1 = b[sidx<T>(k)];
-      const cplx<T> z2 = b[sidx<T>((N - k) & (N - 1))];
-      // P = (Z(k) + conj Z(N-k))/2, Q = (Z(k) - conj Z(N-k))/(2i)
-      P = mk<T>((z1.x + z2.x) * h, (z1.y - z2.y) * h);
-      Q = mk<T>((z1.y + z2.y) * h, (z2.x - z1.x) * h);
-    }
-    da[rowoff + k] = P;
-    if (db) db[rowoff + k] = Q;
-  }
-  w ^= 1;
-}
-
-// The same two row helpers with the length N = 2^L fixed at compile time
-// (G = N/8), for the stage kernels' specialised bodies.
 template <typename T, int L>
 __device__ __forceinline__ void load_pair_spectrum_ct(cplx<T> (&x)[8], const cplx<T>* __restrict__ ma,
                                                       const cplx<T>* __restrict__ mb, long long rowoff, int j,
@@ -272,6 +222,9 @@ __device__ __forceinline__ void load_pair_spectrum_ct(cplx<T> (&x)[8], const cpl
   }
 }
 
+// Spectrum Z of p + i q held at the thread's positions -> kx in [0, KXP)
+// halves of p and q, scaled by 1/N, into row `rowoff` of mixed fields da and
+// db (db null: p only).  One exchange through the free buffer.
 template <typename T, int L, int SYNC>
 __device__ __forceinline__ void store_pair_spectrum_ct(const cplx<T> (&x)[8], cplx<T>* buf0, cplx<T>* buf1, int& w,
                                                        cplx<T>* __restrict__ da, cplx<T>* __restrict__ db,

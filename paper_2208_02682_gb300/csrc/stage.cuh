@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_inv(const Ru
     }
     cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
     int w = 0;
-    gfft<T, +1, L, 2, true>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
+    gfft<T, +1, L, 2, false>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
     cplx<T>* dst = d.mix + (long long)o * d.g.mi + kx;
 #pragma unroll
     for (int m = 0; m < 8; ++m) dst[(j + m * G) * KXP] = x[m];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_fwd(const Ru
     for (int m = 0; m < 8; ++m) x[m] = src[(j + m * G) * KXP];
     cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw) + (size_t)c * col_buf_stride<T>(N, C);
     int w = 0;
-    gfft<T, -1, L, 2, true>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
+    gfft<T, -1, L, 2, false>(x, b0, b0 + row_stride<T>(N), w, j, 0, d.tw);
     const T inv = (T)1 / (T)N;
     cplx<T>* dst = d.ps + (long long)p * d.g.ms + kx;
 #pragma unroll
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_stage_phys_q(const RunDesc<T>* __restri
 // ---------------------------------------------------------------------------
 // a2: row pass with products.  Local block = (pair group, row block): Bp rows
 // and product pairs [pg*ppb, (pg+1)*ppb), with Wp groups of G = N/8 threads
-// per row.  Every transform stays in the registers of its group (group_fft):
+// per row.  Every transform stays in the registers of its group (gfft):
 // a row's physical values live at the thread's own positions x = j + m G,
 // where the products are formed and the forward transform of each product
 // pair starts.  First the row's base fields (u, v, h, zeta; Strategy 2: xi),
