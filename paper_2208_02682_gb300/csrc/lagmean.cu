@@ -372,7 +372,7 @@ static void fill_desc(sw_handle* h, RunDesc<T>& d, int ppb) {
   d.nb[KT_PHYS_Q] = (L.np > 0 && L.strategy == 2 && L.has_q) ? (int)((g.np + 255) / 256) : 0;
   d.nb[KT_ROW_PROD] = L.np > 0 ? (g.N / h->Bp) * ((npairs + ppb - 1) / ppb) : 0;
   d.nb[KT_COL_FWD] = L.np > 0 ? ntile * L.np : 0;
-  d.nb[KT_UPDATE] = (int)((g.ms + UPD_MODES - 1) / UPD_MODES) * L.nf;
+  d.nb[KT_UPDATE] = (int)((g.ms + update_modes(g.N) - 1) / update_modes(g.N)) * L.nf;
 }
 
 // Build (or rebuild) the descriptor table of a batch from its members.
