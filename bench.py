@@ -368,7 +368,9 @@ def measure_large_grids(lm, torch, sizes=(1024, 2048), steps=4, graph_steps=8):
         step_ms = e0.elapsed_time(e1) / graph_steps
         kt = lm.sw_kernel_times(h, steps)
         lm.sw_destroy(h)
-        per = {k: {"ms_per_launch": t / c, "launches": c, "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9,
+        per = {k: {"ms_per_launch": t / c, "launches": c, "algorithmic_bytes": b / c,
+                   "dram_bytes": measured_traffic(k, N),
+                   "GBps_algorithmic": (b / c) / (t / c * 1e-3) / 1e9,
                    "frac": (b / c) / (t / c * 1e-3) / 1e9 / peak}
                for k, (t, c, b) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
         dom = max(kt, key=lambda k: kt[k][0])
@@ -645,8 +647,17 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024, 2048), 
 # (dram__bytes_read.sum + dram__bytes_write.sum) summarised in profiles/;
 # keyed by (kernel, N).  Valid only while the stage-kernel sources are those
 # of the captures (their hash below); otherwise `traffic` is reported null.
-TRAFFIC_CAPTURES = {}
-TRAFFIC_SOURCES_SHA256 = None
+TRAFFIC_CAPTURES = {
+    # bench workload (256^2, S1 + S2 batch): warm L2 as in the timed run, mean of
+    # five captured launches (each covering both runs) halved
+    ("row_prod", 256): 133_197,
+    # FP32 Strategy 1 (zeta, h, u, v, positions, Eulerian), one launch, cold caches
+    ("row_prod", 1024): 52_690_000, ("col_inv", 1024): 18_020_000, ("col_fwd", 1024): 31_110_000,
+    ("update", 1024): 54_430_000, ("row_inv", 1024): 11_410_000,
+    ("row_prod", 2048): 291_900_000, ("col_inv", 2048): 192_900_000, ("col_fwd", 2048): 174_600_000,
+    ("update", 2048): 380_700_000, ("row_inv", 2048): 58_100_000,
+}
+TRAFFIC_SOURCES_SHA256 = "080fa51237e1f9cbb4a44b06adcd25510c6b917a7a73370e0de9fbdc2fc95d55"
 
 
 # the sources that define the stage kernels and their launch shapes
@@ -869,9 +880,20 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, precision and served figures")
     ap.add_argument("--serve-jobs", type=int, default=24,
                     help="requests in the served stream (the full serving form is 200)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the served stream (--serve-jobs requests) and print its JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        import torch
+        torch.cuda.set_device(dist_env()[2])
+        import paper_2208_02682_gb300 as lm
+        lm.build()
+        clk = ClockSampler(dist_env()[2])
+        clk.start()
+        served = measure_served(lm, n_jobs=args.serve_jobs)
+        print(json.dumps({"served": served, "clocks": clk.stop()}), flush=True)
     else:
         run_ours(args)
 
