@@ -317,6 +317,11 @@ struct BatchExec {
   int nstages = 4;  // stage passes per step of the members' (common) stepper
   int stepper = SW_STEP_RK4;
   bool warp = false;  // every member's N <= 256: row kernels without named barriers
+  // pipelined column forward pass (FP32 members all of one size N >= 1024):
+  // log2 N, persistent blocks and shared memory; 0: one tile per block
+  int pipeL = 0;
+  int pipe_grid = 0;
+  size_t pipe_smem = 0;
   std::string err;
 };
 
@@ -436,6 +441,28 @@ static int batch_build_t(BatchExec* b) {
       for (int st = 0; st < 4; ++st) b->bytes[k][st] += (k == KT_UPDATE ? kb.update[st] : by[k]);
     }
   }
+  // large FP32 grids of one size: a persistent column forward pass that
+  // stages the next tile while transforming the current one
+  b->pipeL = 0;
+  if (sizeof(T) == 4 && n > 0 && b->members[0]->g.N >= 1024) {
+    const int N0 = b->members[0]->g.N;
+    bool same = true;
+    for (int r = 0; r < n; ++r) same = same && b->members[r]->g.N == N0 && b->members[r]->lC == 2;
+    int dev = 0, nsm = 0;
+    const int total = b->start[(size_t)KT_COL_FWD * (n + 1) + n];
+    if (same && total > 0 && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+      const int L = b->members[0]->g.log2N;
+      const size_t sm = col_fwd_pipe_smem(N0);
+      const int occ = col_fwd_pipe_occupancy(L, b->threads[KT_COL_FWD], sm);
+      if (occ >= 1) {
+        b->pipeL = L;
+        b->pipe_grid = total < nsm * occ ? total : nsm * occ;
+        b->pipe_smem = sm;
+      }
+    }
+    cudaGetLastError();
+  }
   const size_t desc_bytes = (sizeof(RunDesc<T>) * n + 255) & ~(size_t)255;
   const size_t need = desc_bytes + sizeof(int) * b->start.size();
   if (need > b->table_bytes) {
@@ -504,6 +531,12 @@ static cudaError_t enqueue_batch_step(BatchExec* b, cudaStream_t s, Prof* pf, in
       if (commit_only && k != KT_UPDATE) continue;
       const int total = b->start[(size_t)k * (n + 1) + n];
       if (total == 0) continue;
+      if (b->pipeL && k == KT_COL_FWD) {
+        LAUNCH(SW_K_OF_KT[k], b->bytes[k][stage],
+               launch_col_fwd_pipe(b->pipeL, (const RunDesc<float>*)b->d_table, b->d_start + (size_t)k * (n + 1), n,
+                                   b->pipe_grid, b->threads[k], b->pipe_smem, total, pf == nullptr, s));
+        continue;
+      }
       LAUNCH(SW_K_OF_KT[k], b->bytes[k][stage],
              launch_stage<T>(k, runs, b->d_start + (size_t)k * (n + 1), n, total, b->threads[k], b->smem[k], stage,
                              b->warp, pf == nullptr, s));

@@ -58,6 +58,13 @@ template <typename T> cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStr
 template <typename T>
 cudaError_t launch_stage(int kt, const RunDesc<T>* runs, const int* start, int nruns, int blocks, int threads,
                          size_t smem, int stage, bool warp, bool pdl, cudaStream_t s);
+// Pipelined column forward pass of the large FP32 grids (L = log2 N in
+// {10, 11}, four-column tiles): `blocks` persistent blocks over `total`
+// work items.
+cudaError_t launch_col_fwd_pipe(int L, const RunDesc<float>* runs, const int* start, int nruns, int blocks,
+                                int threads, size_t smem, int total, bool pdl, cudaStream_t s);
+// Resident blocks per SM of a pipelined column forward launch (0 on error).
+int col_fwd_pipe_occupancy(int L, int threads, size_t smem);
 template <typename T>
 cudaError_t launch_spec_to_f64(const cplx<T>* y, const cplx<T>* comp, double2* out, long long ms, int fa, int fb,
                                double scale, cudaStream_t s);

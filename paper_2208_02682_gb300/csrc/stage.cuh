@@ -187,6 +187,99 @@ __global__ void __launch_bounds__(col_max_threads<T>()) k_stage_col_fwd(const Ru
   pdl_release();
 }
 
+// ---------------------------------------------------------------------------
+// Column forward pass of the large grids (FP32, N = 2^L >= 1024, tiles of
+// C = 4 columns: C N/8 = 512 or 1024 threads, two or one blocks per SM).
+// With one or two blocks per SM the loads of a tile and the butterflies of
+// the previous one cannot overlap across blocks, so this pass is
+// persistent: block b takes the launch's work items b, b + gridDim.x, ...
+// (an item is the local block of k_stage_col_fwd: (product, tile) of one
+// run), and while it transforms one item, the next item's mixed tile is
+// copied into shared memory with cp.async (16-byte copies, completed by the
+// group wait before the tile is read).  The arithmetic is that of
+// k_stage_col_fwd, element for element.  (The same staging for the column
+// inverse pass, whose time is set by its 16 output writes rather than its
+// reads, measured no faster and is not used.)
+// Smem: C exchange-buffer pairs (col_buf_stride), then the staged tile of
+// N rows x C complex.
+constexpr int PIPE_C = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy the mixed tile of work item `item` (N rows x 4 complex, row stride
+// KXP) into the staging buffer.
+__device__ __forceinline__ void pipe_stage(float2* st, const RunDesc<float>* __restrict__ runs,
+                                           const int* __restrict__ start, int nruns, int item) {
+  const int r = find_run(start, nruns, item);
+  const RunDesc<float>& d = runs[r];
+  const int lb = item - start[r];
+  const int ntile = d.g.KXP / PIPE_C;
+  const int p = lb / ntile, tile = lb - p * ntile;
+  const float2* src = d.pmix + (long long)p * d.g.mi + tile * PIPE_C;
+  const int rows = d.g.N, KXP = d.g.KXP;
+  for (int q = threadIdx.x; q < 2 * rows; q += blockDim.x) {
+    const int row = q >> 1, half = q & 1;
+    cp_async16(st + row * PIPE_C + half * 2, src + (long long)row * KXP + half * 2);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024, 1) k_stage_col_fwd_pipe(const RunDesc<float>* __restrict__ runs,
+                                                                const int* __restrict__ start, int nruns,
+                                                                int total) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int N = 1 << L, G = N / 8, C = PIPE_C;
+  float2* xb = reinterpret_cast<float2*>(smem_raw);
+  float2* st = xb + (size_t)C * col_buf_stride<float>(N, C);
+  const int c = threadIdx.x & (C - 1), j = threadIdx.x >> 2;
+  float2* b0 = xb + (size_t)c * col_buf_stride<float>(N, C);
+  pdl_wait();  // state written by the previous kernels: only after this
+  int item = blockIdx.x;
+  if (item < total) pipe_stage(st, runs, start, nruns, item);
+  cp_async_commit();
+  int w = 0;
+  for (; item < total; item += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();  // the staged tile is complete and the last transform's buffers are free
+    const int r = find_run(start, nruns, item);
+    const RunDesc<float>& d = runs[r];
+    const int K = d.g.K, KXP = d.g.KXP;
+    const int lb = item - start[r];
+    const int ntile = KXP / C;
+    const int p = lb / ntile, tile = lb - p * ntile;
+    const int kx = tile * C + c;
+    float2 x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = st[(j + m * G) * C + c];
+    __syncthreads();  // every thread has read the staged tile
+    if (item + gridDim.x < total) pipe_stage(st, runs, start, nruns, item + gridDim.x);
+    cp_async_commit();
+    gfft<float, -1, L, 2, false>(x, b0, b0 + row_stride<float>(N), w, j, 0, d.tw);
+    const float inv = 1.0f / (float)N;
+    float2* dst = d.ps + (long long)p * d.g.ms + kx;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = j + m * G;
+      if (k <= K || k >= N - K) {
+        const int ky = k <= K ? k : k - N;
+        dst[(ky + K) * KXP] = kx <= K ? cscale<float>(x[m], inv) : mk<float>(0, 0);
+      }
+    }
+  }
+  cp_async_wait_all();
+  pdl_release();
+}
+
+// Shared memory of a pipelined column forward launch.
+inline size_t col_fwd_pipe_smem(int N) {
+  return ((size_t)PIPE_C * col_buf_stride<float>(N, PIPE_C) + (size_t)N * PIPE_C) * sizeof(float2);
+}
+
 // a3: Strategy-2 gather buffer (physical u, v | h, zeta), local block =
 // (pair, row block of Bi rows, one row per group of N/8 threads).
 template <typename T, bool WARP>
