@@ -650,14 +650,14 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024, 2048), 
 TRAFFIC_CAPTURES = {
     # bench workload (256^2, S1 + S2 batch): warm L2 as in the timed run, mean of
     # five captured launches (each covering both runs) halved
-    ("row_prod", 256): 133_197,
+    ("row_prod", 256): 143_974,
     # FP32 Strategy 1 (zeta, h, u, v, positions, Eulerian), one launch, cold caches
-    ("row_prod", 1024): 52_690_000, ("col_inv", 1024): 18_020_000, ("col_fwd", 1024): 31_110_000,
-    ("update", 1024): 54_430_000, ("row_inv", 1024): 11_410_000,
-    ("row_prod", 2048): 291_900_000, ("col_inv", 2048): 192_900_000, ("col_fwd", 2048): 174_600_000,
-    ("update", 2048): 380_700_000, ("row_inv", 2048): 58_100_000,
+    ("row_prod", 1024): 52_700_000, ("col_inv", 1024): 18_000_000, ("col_fwd", 1024): 31_000_000,
+    ("update", 1024): 54_400_000, ("row_inv", 1024): 11_400_000,
+    ("row_prod", 2048): 291_500_000, ("col_inv", 2048): 193_500_000, ("col_fwd", 2048): 168_600_000,
+    ("update", 2048): 381_500_000, ("row_inv", 2048): 58_000_000,
 }
-TRAFFIC_SOURCES_SHA256 = "080fa51237e1f9cbb4a44b06adcd25510c6b917a7a73370e0de9fbdc2fc95d55"
+TRAFFIC_SOURCES_SHA256 = "6b76c5861ec35611a61d8cfcfc8c6f75ad52a60db08c3a2aeb1fe3e706ffe538"
 
 
 # the sources that define the stage kernels and their launch shapes
