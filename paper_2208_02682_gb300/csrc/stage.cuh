@@ -657,21 +657,22 @@ __device__ __forceinline__ void commit_mode(const RunDesc<T>& d, int f, long lon
 // Right-hand side and RK4 update of evolved field f at mode m = kyi*KXP + kx
 // (kx <= K); prod(p) returns the spectral product p at this mode.
 template <typename T, typename PF>
-__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd, bool even, int f, long long m,
+__device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd, bool even, int f, int m,
                                             int kx, int kyi, PF prod) {
   const Geom& g = d.g;
   const Layout& L = d.L;
   const int st = d.c.stepper;
+  const int msi = (int)g.ms;
   const int role = L.frole[f], slot = L.fslot[f];
   // two-dimensional Euler model: u and v follow zeta (written with it)
   const bool e2 = L.model == 2;
   if (e2 && (role == R_U || role == R_V)) return;
   const int cls = L.fclass[f];
-  const T E = cls == IF_NONE ? (T)1 : d.ef[3 * cls * g.ms + m];
+  const T E = cls == IF_NONE ? (T)1 : d.ef[3 * cls * msi + m];
   // E^2 = e2h + e2l for the commit of y_{n+1} (read where it is committed)
-  auto e2h = [&]() { return cls == IF_NONE ? (T)1 : d.ef[(3 * cls + 1) * g.ms + m]; };
-  auto e2l = [&]() { return cls == IF_NONE ? (T)0 : d.ef[(3 * cls + 2) * g.ms + m]; };
-  const long long o = f * g.ms + m;
+  auto e2h = [&]() { return cls == IF_NONE ? (T)1 : d.ef[(3 * cls + 1) * msi + m]; };
+  auto e2l = [&]() { return cls == IF_NONE ? (T)0 : d.ef[(3 * cls + 2) * msi + m]; };
+  const int o = f * msi + m;
   const T kxf = (T)kx, kyf = (T)(kyi - g.K);
   // xi-first scheme (Strategy 2, forward Euler): xi steps by 2 dt on even
   // steps, gbar on odd ones (integrating factor over 2 dt: E^4)
@@ -705,16 +706,16 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
       if (role == R_H) {
         rhs = csub<T>(mk<T>(0, 0), cadd<T>(cik<T>(prod(L.p_hu), kxf), cik<T>(prod(L.p_hv), kyf)));
       } else {
-        const cplx<T> hh = yin[L.f_h * g.ms + m];
+        const cplx<T> hh = yin[L.f_h * msi + m];
         const cplx<T> Bq = cadd<T>(cscale<T>(hh, d.cc2), prod(L.p_ke));
         if (role == R_U)
-          rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * g.ms + m], d.cf0), prod(L.p_zv)), cik<T>(Bq, kxf));
+          rhs = csub<T>(cadd<T>(cscale<T>(yin[L.f_v * msi + m], d.cf0), prod(L.p_zv)), cik<T>(Bq, kxf));
         else
-          rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * g.ms + m], -d.cf0), prod(L.p_zu)), cik<T>(Bq, kyf));
+          rhs = csub<T>(csub<T>(cscale<T>(yin[L.f_u * msi + m], -d.cf0), prod(L.p_zu)), cik<T>(Bq, kyf));
       }
     } else {
       const T kc = kxf * d.cadvx + kyf * d.cadvy;
-      rhs = cik<T>(yin[f * g.ms + m], -kc);
+      rhs = cik<T>(yin[f * msi + m], -kc);
     }
   } else if (role == R_P) {
     const cplx<T> pp = prod(L.p_p[slot]);
@@ -725,7 +726,7 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
         const bool k0 = (kx == 0 && kyi == g.K);
         ua = mk<T>(k0 ? (slot == 0 ? d.cadvx : d.cadvy) : (T)0, 0);
       } else {
-        ua = yin[(slot == 0 ? L.f_u : L.f_v) * g.ms + m];
+        ua = yin[(slot == 0 ? L.f_u : L.f_v) * msi + m];
       }
       rhs = csub<T>(cscale<T>(ua, (T)sd), pp);
     } else {
@@ -736,11 +737,11 @@ __device__ __forceinline__ void update_mode(const RunDesc<T>& d, int stage, T sd
     const int sc = L.lmf[slot];
     cplx<T> fh;
     if (sc == LMF_ZETA)
-      fh = e2 ? yin[L.f_h * g.ms + m]  // the evolved vorticity (its mean included)
-              : csub<T>(cik<T>(yin[L.f_v * g.ms + m], kxf), cik<T>(yin[L.f_u * g.ms + m], kyf));
-    else if (sc == LMF_H) fh = yin[L.f_h * g.ms + m];
-    else if (sc == LMF_U) fh = yin[L.f_u * g.ms + m];
-    else if (sc == LMF_V) fh = yin[L.f_v * g.ms + m];
+      fh = e2 ? yin[L.f_h * msi + m]  // the evolved vorticity (its mean included)
+              : csub<T>(cik<T>(yin[L.f_v * msi + m], kxf), cik<T>(yin[L.f_u * msi + m], kyf));
+    else if (sc == LMF_H) fh = yin[L.f_h * msi + m];
+    else if (sc == LMF_U) fh = yin[L.f_u * msi + m];
+    else if (sc == LMF_V) fh = yin[L.f_v * msi + m];
     else fh = prod(L.p_q);
     if (role == R_E) {
       rhs = fh;  // Eq. (ave)
@@ -804,17 +805,25 @@ __global__ void __launch_bounds__(256, update_min_blocks<T>()) k_stage_update(co
   const bool even = L.scheme == SCHEME_XI_FIRST ? ((*d.ctr & 1LL) == 0) : true;
   auto modes = [&](auto Uc) {
     constexpr int NU = decltype(Uc)::value;
+    // element offsets of a run fit in 32 bits (16 fields x 933,465 modes at
+    // 2048^2); the mode's (ky, kx) advance by 256 modes per step without a
+    // division each
+    const int msi = (int)g.ms, KXP = g.KXP;
+    int mi = (int)m0;
+    int kyi = mi / KXP, kx = mi - kyi * KXP;
+    const int dq = 256 / KXP, dr = 256 - dq * KXP;
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
-      const long long m = m0 + u * 256;
-      if (m < g.ms) {
-        // modes of a run fit in 32 bits: 32-bit division (64-bit division is a
-        // long software sequence)
-        const int mi = (int)m;
-        const int kyi = mi / g.KXP, kx = mi - kyi * g.KXP;
-        if (kx <= g.K) {
-          update_mode<T>(d, stage, sd, even, f, m, kx, kyi, [&](int p) { return d.ps[(long long)p * g.ms + m]; });
-        }
+      if (mi < msi && kx <= g.K) {
+        const int mm = mi;
+        update_mode<T>(d, stage, sd, even, f, mm, kx, kyi, [&](int p) { return d.ps[p * msi + mm]; });
+      }
+      mi += 256;
+      kx += dr;
+      kyi += dq;
+      if (kx >= KXP) {
+        kx -= KXP;
+        ++kyi;
       }
     }
   };
