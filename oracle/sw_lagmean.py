@@ -54,8 +54,13 @@ the real inverse transform).
 Parity pins (tests/test_oracle_*.py): closed forms for a uniform inertial
 oscillation, uniform advection and the Stokes drift of a small Poincare wave,
 linear dispersion, exact mass conservation, fourth-order energy drift, PV
-material conservation, agreement of Strategies 1 and 2, and brute-force
-particle tracking with trajectory averaging (``oracle.particles``).
+material conservation, agreement of Strategies 1 and 2, brute-force particle
+tracking with trajectory averaging (``oracle.particles``), and Strategy 2's
+uniform-flow closed form under every stepper (which pins the s = 0 limit
+under forward Euler).  Parity unpinned: in the "xi_first" scheme, the time
+level of gbar's advecting velocity (xi_{m+1}/s_{m+1}); the scheme itself is
+pinned by its uniform-flow closed form and its first-order convergence, but
+other consistent levels would pass those too.
 """
 from __future__ import annotations
 
