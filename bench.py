@@ -650,14 +650,14 @@ def measure_served(lm, n_jobs=24, rate=50.0, sizes=(128, 256, 512, 1024, 2048), 
 TRAFFIC_CAPTURES = {
     # bench workload (256^2, S1 + S2 batch): warm L2 as in the timed run, mean of
     # five captured launches (each covering both runs) halved
-    ("row_prod", 256): 143_974,
+    ("row_prod", 256): 150_963,
     # FP32 Strategy 1 (zeta, h, u, v, positions, Eulerian), one launch, cold caches
-    ("row_prod", 1024): 52_700_000, ("col_inv", 1024): 18_000_000, ("col_fwd", 1024): 31_000_000,
-    ("update", 1024): 54_400_000, ("row_inv", 1024): 11_400_000,
-    ("row_prod", 2048): 291_500_000, ("col_inv", 2048): 193_500_000, ("col_fwd", 2048): 168_600_000,
-    ("update", 2048): 381_500_000, ("row_inv", 2048): 58_000_000,
+    ("row_prod", 1024): 52_500_000, ("col_inv", 1024): 17_800_000, ("col_fwd", 1024): 31_000_000,
+    ("update", 1024): 55_600_000, ("row_inv", 1024): 11_400_000,
+    ("row_prod", 2048): 291_800_000, ("col_inv", 2048): 193_200_000, ("col_fwd", 2048): 168_000_000,
+    ("update", 2048): 387_200_000, ("row_inv", 2048): 58_000_000,
 }
-TRAFFIC_SOURCES_SHA256 = "6b76c5861ec35611a61d8cfcfc8c6f75ad52a60db08c3a2aeb1fe3e706ffe538"
+TRAFFIC_SOURCES_SHA256 = "fa76517f9aaad40a3c3e75365a13ecdd0fdd7afdae7108cebdd0f27f98c4b8f6"
 
 
 # the sources that define the stage kernels and their launch shapes
