@@ -194,3 +194,13 @@ def test_project_static_rejects_bad_buffers_before_any_launch(lm, case):
 
 def test_batch_shape_setter_rejects_null(lm):
     assert lm.api.load().sw_batch_set_shape(None, 0) == lm.api.SW_EINVAL
+
+
+def test_fma_peak_rejects_bad_arguments(lm):
+    lib = lm.api.load()
+    import ctypes as C
+    t = C.c_double(0.0)
+    assert lib.sw_fma_peak(7, 16, C.byref(t), None) == lm.api.SW_EINVAL
+    assert lib.sw_fma_peak(lm.api.SW_PREC_FP64, 0, C.byref(t), None) == lm.api.SW_EINVAL
+    assert lib.sw_fma_peak(lm.api.SW_PREC_FP32, 16, None, None) == lm.api.SW_EINVAL
+    assert "sw_fma_peak" in lm.sw_last_error(None)
